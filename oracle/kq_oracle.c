@@ -1,0 +1,637 @@
+/*
+ * kq_oracle.c -- plain FP64 CPU reference for exact k-means colour quantization
+ * (Weighted Sort-Means, Celebi 2011).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the benchmark's
+ * CPU-baseline leg may load this library.  It shares no code, header, table or
+ * helper with the CUDA path; the two agree only through the paper and the
+ * written readings below.
+ *
+ * Because the paper states that Weighted Sort-Means gives the same result as
+ * conventional k-means from the same centres (Section 2.2), the oracle is the
+ * plain definition: dense weighted Lloyd over the unique colours, every distance
+ * in FP64, every sum an exact 64-bit integer.  Nothing here is blocked, fused or
+ * reordered.
+ *
+ * Readings where the paper is silent (each one is also listed in the design notes):
+ *  - colours are 24-bit keys (R<<16)|(G<<8)|B; the unique colours are kept in
+ *    ascending key order;
+ *  - weights are integer pixel counts (the paper divides them by N; centres and
+ *    the relative convergence test do not change under that scaling);
+ *  - ties in every argmin go to the lowest centre index;
+ *  - an empty cluster keeps its previous centre;
+ *  - SSE_i is the weighted SSE of iteration i's assignment against the centres
+ *    that entered iteration i; the run stops after iteration i when
+ *    SSE_i == 0 or (i > 1 and (SSE_{i-1} - SSE_i) / SSE_i <= eps); eps < 0
+ *    disables the test (a fixed number of iterations, as in Section 3.2);
+ *  - when K >= N' every scheme returns the N' unique colours in key order and
+ *    fills the remaining centres with copies of the last one;
+ *  - random draws use the counter-based SplitMix64 stream defined at
+ *    or_rand() and the integer range reduction of or_below().
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_API __attribute__((visibility("default")))
+
+enum { OR_FGY = 0, OR_LBG = 1, OR_MMX = 2, OR_DEN = 3, OR_VAR = 4, OR_SFF = 5, OR_KPP = 6 };
+
+/* ------------------------------------------------------------------------- */
+/* Random numbers: SplitMix64 (Steele, Lea and Flood, OOPSLA 2014).  The n-th  */
+/* output of the generator seeded with s is mix(s + n * gamma).  Stream `st`   */
+/* counter `i` is output number n = st * 2^32 + i + 1.                         */
+/* ------------------------------------------------------------------------- */
+OR_API uint64_t or_rand(uint64_t seed, uint32_t stream, uint32_t ctr)
+{
+    uint64_t n = ((uint64_t)stream << 32) + (uint64_t)ctr + 1u;
+    uint64_t z = seed + n * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+/* An integer in [0, m): the high 64 bits of the 128-bit product u * m. */
+OR_API uint64_t or_below(uint64_t u, uint64_t m)
+{
+    return (uint64_t)(((unsigned __int128)u * (unsigned __int128)m) >> 64);
+}
+
+static void key_rgb(uint32_t key, int64_t *r, int64_t *g, int64_t *b)
+{
+    *r = (key >> 16) & 255u;
+    *g = (key >> 8) & 255u;
+    *b = key & 255u;
+}
+
+static int64_t key_dist2(uint32_t a, uint32_t b)
+{
+    int64_t ar, ag, ab, br, bg, bb;
+    key_rgb(a, &ar, &ag, &ab);
+    key_rgb(b, &br, &bg, &bb);
+    return (ar - br) * (ar - br) + (ag - bg) * (ag - bg) + (ab - bb) * (ab - bb);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Unique-colour sampling with weights (Section 2.2, items 1 and 2): a count   */
+/* per 24-bit colour, then the colours with a nonzero count in ascending key   */
+/* order.  Returns N'; writes at most `cap` entries.                           */
+/* ------------------------------------------------------------------------- */
+OR_API int64_t or_histogram(const uint8_t *rgb, int64_t n, uint32_t *keys, uint32_t *weights, int64_t cap)
+{
+    uint32_t *cnt = (uint32_t *)calloc((size_t)1 << 24, sizeof(uint32_t));
+    if (!cnt) return -1;
+    for (int64_t i = 0; i < n; ++i) {
+        uint32_t key = ((uint32_t)rgb[3 * i] << 16) | ((uint32_t)rgb[3 * i + 1] << 8) | rgb[3 * i + 2];
+        cnt[key] += 1u;
+    }
+    int64_t u = 0;
+    for (uint32_t key = 0; key < (1u << 24); ++key) {
+        if (cnt[key]) {
+            if (u < cap) {
+                keys[u] = key;
+                weights[u] = cnt[key];
+            }
+            ++u;
+        }
+    }
+    free(cnt);
+    return u;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Assignment step (Algorithm 1, the argmin over all K centres; Algorithm 2    */
+/* reaches the same labels).  Squared Euclidean distance in FP64, lowest index */
+/* on ties.  d1/d2 (nullable) receive the best and second-best distances.      */
+/* Returns the weighted SSE of Eq. 1 for this assignment.                      */
+/* ------------------------------------------------------------------------- */
+OR_API double or_assign(const uint32_t *keys, const uint32_t *w, int64_t n, int K, const double *c,
+                        uint8_t *labels, double *d1, double *d2)
+{
+    double sse = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t r, g, b;
+        key_rgb(keys[i], &r, &g, &b);
+        double best = INFINITY, second = INFINITY;
+        int arg = 0;
+        for (int k = 0; k < K; ++k) {
+            double dr = (double)r - c[3 * k], dg = (double)g - c[3 * k + 1], db = (double)b - c[3 * k + 2];
+            double d = dr * dr + dg * dg + db * db;
+            if (d < best) {
+                second = best;
+                best = d;
+                arg = k;
+            } else if (d < second) {
+                second = d;
+            }
+        }
+        labels[i] = (uint8_t)arg;
+        if (d1) d1[i] = best;
+        if (d2) d2[i] = second;
+        sse += (double)w[i] * best;
+    }
+    return sse;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Update step (Algorithm 2, the weighted mean of each cluster): exact int64   */
+/* sums S_k = sum w*x and W_k = sum w, then c_k = S_k / W_k in FP64.  An empty */
+/* cluster keeps its centre.  sums (nullable) receives K x {S_r,S_g,S_b,W}.    */
+/* ------------------------------------------------------------------------- */
+OR_API void or_update(const uint32_t *keys, const uint32_t *w, int64_t n, int K, const uint8_t *labels,
+                      const double *c_in, double *c_out, int64_t *sums)
+{
+    int64_t *s = (int64_t *)calloc((size_t)K * 4, sizeof(int64_t));
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t r, g, b;
+        key_rgb(keys[i], &r, &g, &b);
+        int k = labels[i];
+        s[4 * k + 0] += (int64_t)w[i] * r;
+        s[4 * k + 1] += (int64_t)w[i] * g;
+        s[4 * k + 2] += (int64_t)w[i] * b;
+        s[4 * k + 3] += (int64_t)w[i];
+    }
+    for (int k = 0; k < K; ++k) {
+        if (s[4 * k + 3] > 0) {
+            for (int ch = 0; ch < 3; ++ch) c_out[3 * k + ch] = (double)s[4 * k + ch] / (double)s[4 * k + 3];
+        } else {
+            for (int ch = 0; ch < 3; ++ch) c_out[3 * k + ch] = c_in[3 * k + ch];
+        }
+    }
+    if (sums) memcpy(sums, s, (size_t)K * 4 * sizeof(int64_t));
+    free(s);
+}
+
+/* Convergence test of Section 3.3 (Linde, Buzo and Gray): relative SSE drop. */
+static int converged_after(int iter, double prev, double cur, double eps)
+{
+    if (eps < 0.0) return 0;
+    if (cur == 0.0) return 1;
+    if (iter <= 1) return 0;
+    return (prev - cur) / cur <= eps;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Weighted Lloyd (Algorithm 2 without the pruning, which leaves the result    */
+/* unchanged).  centers: in = seeds, out = final.  labels: the last            */
+/* assignment.  sse_hist (nullable, max_iter entries).  Returns the number of  */
+/* iterations run; *converged is set when the relative test fired.             */
+/* ------------------------------------------------------------------------- */
+OR_API int or_lloyd(const uint32_t *keys, const uint32_t *w, int64_t n, int K, double *centers, double eps,
+                    int max_iter, uint8_t *labels, double *sse_hist, int *converged, int64_t *sums)
+{
+    double *next = (double *)malloc(sizeof(double) * 3 * (size_t)K);
+    double prev = 0.0;
+    int it = 0;
+    if (converged) *converged = 0;
+    while (it < max_iter) {
+        double sse = or_assign(keys, w, n, K, centers, labels, NULL, NULL);
+        ++it;
+        if (sse_hist) sse_hist[it - 1] = sse;
+        or_update(keys, w, n, K, labels, centers, next, sums);
+        memcpy(centers, next, sizeof(double) * 3 * (size_t)K);
+        if (converged_after(it, prev, sse, eps)) {
+            if (converged) *converged = 1;
+            break;
+        }
+        prev = sse;
+    }
+    free(next);
+    return it;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Palette: each centre rounded half-up to 0..255.  For a cluster with pixels  */
+/* this is floor((2 S + W) / (2 W)) in exact integers; for an empty cluster it */
+/* is floor(c + 0.5) of the held centre, clamped.                              */
+/* ------------------------------------------------------------------------- */
+OR_API void or_palette(const int64_t *sums, const double *c, int K, uint8_t *pal)
+{
+    for (int k = 0; k < K; ++k) {
+        int64_t W = sums ? sums[4 * k + 3] : 0;
+        for (int ch = 0; ch < 3; ++ch) {
+            int64_t v;
+            if (W > 0) {
+                v = (2 * sums[4 * k + ch] + W) / (2 * W);
+            } else {
+                double f = floor(c[3 * k + ch] + 0.5);
+                v = f < 0.0 ? 0 : (f > 255.0 ? 255 : (int64_t)f);
+            }
+            pal[3 * k + ch] = (uint8_t)v;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Pixel mapping (Section 1: each pixel to its nearest palette colour; Section */
+/* 2.1: a full search of the palette) with integer distances and the lowest    */
+/* index on ties.  sse_num (nullable) = sum of squared errors, the numerator   */
+/* of the MSE of Section 3.1 (Eq. 2).                                          */
+/* ------------------------------------------------------------------------- */
+OR_API void or_map(const uint8_t *rgb, int64_t n, const uint8_t *pal, int K, uint8_t *idx, int64_t *sse_num)
+{
+    int64_t total = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t best = INT64_MAX;
+        int arg = 0;
+        for (int k = 0; k < K; ++k) {
+            int64_t dr = (int64_t)rgb[3 * i] - pal[3 * k];
+            int64_t dg = (int64_t)rgb[3 * i + 1] - pal[3 * k + 1];
+            int64_t db = (int64_t)rgb[3 * i + 2] - pal[3 * k + 2];
+            int64_t d = dr * dr + dg * dg + db * db;
+            if (d < best) {
+                best = d;
+                arg = k;
+            }
+        }
+        idx[i] = (uint8_t)arg;
+        total += best;
+    }
+    if (sse_num) *sse_num = total;
+}
+
+/* ========================================================================= */
+/* Seeding: the generic initialization schemes of Section 2.3.                */
+/* ========================================================================= */
+
+static void centre_from_key(double *c, uint32_t key)
+{
+    int64_t r, g, b;
+    key_rgb(key, &r, &g, &b);
+    c[0] = (double)r;
+    c[1] = (double)g;
+    c[2] = (double)b;
+}
+
+/* Partial Fisher-Yates: the first `count` entries of a uniformly random     */
+/* permutation of 0..n-1, drawn from stream `stream`, written to out.        */
+static void partial_shuffle(int64_t n, int64_t count, uint64_t seed, uint32_t stream, int64_t *out)
+{
+    int64_t *a = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    for (int64_t i = 0; i < n; ++i) a[i] = i;
+    for (int64_t j = 0; j < count; ++j) {
+        int64_t r = j + (int64_t)or_below(or_rand(seed, stream, (uint32_t)j), (uint64_t)(n - j));
+        int64_t t = a[j];
+        a[j] = a[r];
+        a[r] = t;
+        out[j] = a[j];
+    }
+    free(a);
+}
+
+/* Forgy: K distinct data points drawn uniformly (Algorithm 2, first line). */
+static void seed_fgy(const uint32_t *keys, int64_t n, int K, uint64_t seed, double *c)
+{
+    int64_t *pick = (int64_t *)malloc(sizeof(int64_t) * (size_t)K);
+    partial_shuffle(n, K, seed, 1, pick);
+    for (int k = 0; k < K; ++k) centre_from_key(c + 3 * k, keys[pick[k]]);
+    free(pick);
+}
+
+/* Minmax over the points `idx[0..m-1]` (ascending unique-colour indices):   */
+/* the first centre is idx[first]; each next centre is the point whose       */
+/* smallest distance to the chosen centres is largest (lowest index on ties).*/
+static void maxmin_select(const uint32_t *keys, const int64_t *idx, int64_t m, int64_t first, int K, double *c)
+{
+    int64_t *mind = (int64_t *)malloc(sizeof(int64_t) * (size_t)m);
+    int64_t cur = idx[first];
+    centre_from_key(c, keys[cur]);
+    for (int64_t i = 0; i < m; ++i) mind[i] = INT64_MAX;
+    for (int k = 1; k < K; ++k) {
+        int64_t best = -1, arg = 0;
+        for (int64_t i = 0; i < m; ++i) {
+            int64_t d = key_dist2(keys[idx[i]], keys[cur]);
+            if (d < mind[i]) mind[i] = d;
+            if (mind[i] > best) {
+                best = mind[i];
+                arg = i;
+            }
+        }
+        cur = idx[arg];
+        centre_from_key(c + 3 * k, keys[cur]);
+    }
+    free(mind);
+}
+
+/* Minmax (MMX): first centre uniform over the unique colours. */
+static void seed_mmx(const uint32_t *keys, int64_t n, int K, uint64_t seed, double *c)
+{
+    int64_t *idx = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    for (int64_t i = 0; i < n; ++i) idx[i] = i;
+    int64_t first = (int64_t)or_below(or_rand(seed, 3, 0), (uint64_t)n);
+    maxmin_select(keys, idx, n, first, K, c);
+    free(idx);
+}
+
+static int cmp_i64(const void *a, const void *b)
+{
+    int64_t x = *(const int64_t *)a, y = *(const int64_t *)b;
+    return (x > y) - (x < y);
+}
+
+/* Subset size of Subset Farthest First: min(N', max(K, ceil(2 K ln K))). */
+OR_API int64_t or_sff_size(int64_t n, int K)
+{
+    int64_t s = (int64_t)ceil(2.0 * (double)K * log((double)K));
+    if (s < K) s = K;
+    if (s > n) s = n;
+    return s;
+}
+
+/* Subset Farthest First (SFF): minmax on a uniform random subset. */
+static void seed_sff(const uint32_t *keys, int64_t n, int K, uint64_t seed, double *c)
+{
+    int64_t s = or_sff_size(n, K);
+    int64_t *sub = (int64_t *)malloc(sizeof(int64_t) * (size_t)s);
+    partial_shuffle(n, s, seed, 4, sub);
+    qsort(sub, (size_t)s, sizeof(int64_t), cmp_i64);
+    int64_t first = (int64_t)or_below(or_rand(seed, 5, 0), (uint64_t)s);
+    maxmin_select(keys, sub, s, first, K, c);
+    free(sub);
+}
+
+/* K-means++ (KPP): first centre drawn with probability w_i / sum w; centre */
+/* r drawn with probability w_i D(x_i)^2 / sum w D^2, where D is the        */
+/* distance to the nearest chosen centre.  Integer arithmetic throughout:   */
+/* t = below(u, total), choose the first i whose running sum exceeds t.     */
+static void seed_kpp(const uint32_t *keys, const uint32_t *w, int64_t n, int K, uint64_t seed, double *c)
+{
+    int64_t *d2 = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    int64_t total = 0;
+    for (int64_t i = 0; i < n; ++i) total += (int64_t)w[i];
+    int64_t t = (int64_t)or_below(or_rand(seed, 2, 0), (uint64_t)total), run = 0, cur = n - 1;
+    for (int64_t i = 0; i < n; ++i) {
+        run += (int64_t)w[i];
+        if (run > t) {
+            cur = i;
+            break;
+        }
+    }
+    centre_from_key(c, keys[cur]);
+    for (int64_t i = 0; i < n; ++i) d2[i] = INT64_MAX;
+    for (int k = 1; k < K; ++k) {
+        total = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            int64_t d = key_dist2(keys[i], keys[cur]);
+            if (d < d2[i]) d2[i] = d;
+            total += (int64_t)w[i] * d2[i];
+        }
+        t = (int64_t)or_below(or_rand(seed, 2, (uint32_t)k), (uint64_t)total);
+        run = 0;
+        cur = n - 1;
+        for (int64_t i = 0; i < n; ++i) {
+            run += (int64_t)w[i] * d2[i];
+            if (run > t) {
+                cur = i;
+                break;
+            }
+        }
+        centre_from_key(c + 3 * k, keys[cur]);
+    }
+    free(d2);
+}
+
+/* Maximum variance (VAR): the channel of largest pixel-weighted variance     */
+/* (compared exactly as W*sum(w x^2) - (sum w x)^2, ties to R, then G); the   */
+/* unique colours sorted ascending on it (ties by key); K equal-count groups  */
+/* [floor(g N'/K), floor((g+1) N'/K)); each centre is the group's middle     */
+/* element, index floor((lo + hi - 1) / 2).                                  */
+static const uint32_t *g_sort_keys;
+static int g_sort_shift;
+static int cmp_channel(const void *a, const void *b)
+{
+    uint32_t ka = g_sort_keys[*(const int64_t *)a], kb = g_sort_keys[*(const int64_t *)b];
+    uint32_t va = (ka >> g_sort_shift) & 255u, vb = (kb >> g_sort_shift) & 255u;
+    if (va != vb) return va < vb ? -1 : 1;
+    return (ka > kb) - (ka < kb);
+}
+
+OR_API int or_var_channel(const uint32_t *keys, const uint32_t *w, int64_t n)
+{
+    __int128 W = 0, s1[3] = {0, 0, 0}, s2[3] = {0, 0, 0};
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t x[3];
+        key_rgb(keys[i], &x[0], &x[1], &x[2]);
+        W += w[i];
+        for (int ch = 0; ch < 3; ++ch) {
+            s1[ch] += (__int128)w[i] * x[ch];
+            s2[ch] += (__int128)w[i] * x[ch] * x[ch];
+        }
+    }
+    int best = 0;
+    __int128 bv = W * s2[0] - s1[0] * s1[0];
+    for (int ch = 1; ch < 3; ++ch) {
+        __int128 v = W * s2[ch] - s1[ch] * s1[ch];
+        if (v > bv) {
+            bv = v;
+            best = ch;
+        }
+    }
+    return best;
+}
+
+static void seed_var(const uint32_t *keys, const uint32_t *w, int64_t n, int K, double *c)
+{
+    int ch = or_var_channel(keys, w, n);
+    int64_t *ord = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    for (int64_t i = 0; i < n; ++i) ord[i] = i;
+    g_sort_keys = keys;
+    g_sort_shift = 16 - 8 * ch;
+    qsort(ord, (size_t)n, sizeof(int64_t), cmp_channel);
+    for (int g = 0; g < K; ++g) {
+        int64_t lo = (int64_t)g * n / K, hi = (int64_t)(g + 1) * n / K;
+        centre_from_key(c + 3 * g, keys[ord[(lo + hi - 1) / 2]]);
+    }
+    free(ord);
+}
+
+/* Density-based (DEN): 64 uniform cells (4 levels per channel, cell index    */
+/* (R>>6)*16 + (G>>6)*4 + (B>>6)).  Seats are apportioned to cells in          */
+/* proportion to their pixel counts by largest remainder (ties to the lower    */
+/* cell); a cell whose share exceeds its unique-colour count is fixed at that  */
+/* count and the rest is apportioned again among the other cells.  Inside each */
+/* cell the centres are a uniform draw without replacement (stream 16 + cell). */
+OR_API void or_den_quota(const int64_t *cellw, const int64_t *celln, int K, int64_t *q)
+{
+    int fixed[64];
+    memset(fixed, 0, sizeof(fixed));
+    for (;;) {
+        int64_t seats = K, wa = 0;
+        for (int c = 0; c < 64; ++c) {
+            if (fixed[c]) seats -= celln[c];
+            else if (celln[c] > 0) wa += cellw[c];
+        }
+        int64_t rem[64], given = 0;
+        for (int c = 0; c < 64; ++c) {
+            q[c] = 0;
+            rem[c] = -1;
+            if (fixed[c]) {
+                q[c] = celln[c];
+            } else if (celln[c] > 0 && wa > 0) {
+                q[c] = seats * cellw[c] / wa;
+                rem[c] = seats * cellw[c] % wa;
+                given += q[c];
+            }
+        }
+        for (int64_t left = seats - given; left > 0; --left) {
+            int arg = -1;
+            for (int c = 0; c < 64; ++c)
+                if (rem[c] >= 0 && (arg < 0 || rem[c] > rem[arg])) arg = c;
+            q[arg] += 1;
+            rem[arg] = -1;
+        }
+        int grew = 0;
+        for (int c = 0; c < 64; ++c) {
+            if (!fixed[c] && q[c] > celln[c]) {
+                fixed[c] = 1;
+                grew = 1;
+            }
+        }
+        if (!grew) return;
+    }
+}
+
+static int den_cell(uint32_t key)
+{
+    return (int)(((key >> 22) & 3u) * 16u + ((key >> 14) & 3u) * 4u + ((key >> 6) & 3u));
+}
+
+static void seed_den(const uint32_t *keys, const uint32_t *w, int64_t n, int K, uint64_t seed, double *c)
+{
+    int64_t cellw[64], celln[64], q[64];
+    memset(cellw, 0, sizeof(cellw));
+    memset(celln, 0, sizeof(celln));
+    for (int64_t i = 0; i < n; ++i) {
+        int cc = den_cell(keys[i]);
+        cellw[cc] += (int64_t)w[i];
+        celln[cc] += 1;
+    }
+    or_den_quota(cellw, celln, K, q);
+    int k = 0;
+    for (int cc = 0; cc < 64; ++cc) {
+        if (q[cc] == 0) continue;
+        int64_t *members = (int64_t *)malloc(sizeof(int64_t) * (size_t)celln[cc]);
+        int64_t *pick = (int64_t *)malloc(sizeof(int64_t) * (size_t)q[cc]);
+        int64_t m = 0;
+        for (int64_t i = 0; i < n; ++i)
+            if (den_cell(keys[i]) == cc) members[m++] = i;
+        partial_shuffle(m, q[cc], seed, 16u + (uint32_t)cc, pick);
+        for (int64_t j = 0; j < q[cc]; ++j) centre_from_key(c + 3 * (k++), keys[members[pick[j]]]);
+        free(members);
+        free(pick);
+    }
+}
+
+/* Exact per-cluster SSE about the cluster mean, as the fraction num / W with  */
+/* num = W * sum(w |x|^2) - |S|^2.  Used to rank clusters for a partial split. */
+static int sse_greater(__int128 na, int64_t wa, __int128 nb, int64_t wb)
+{
+    /* compare na/wa > nb/wb with wa, wb > 0 (an empty cluster ranks lowest) */
+    if (wa == 0) return 0;
+    if (wb == 0) return 1;
+    /* na * wb and nb * wa stay below 2^127 for images up to 2^26 pixels */
+    return na * (__int128)wb > nb * (__int128)wa;
+}
+
+/* Splitting (LBG): the centroid, then each centre c split into c - eps and    */
+/* c + eps (c - eps keeps index j, c + eps takes index m + j), each round       */
+/* refined by full Lloyd.  When K is not a power of two the last round splits   */
+/* only the K - m clusters of largest weighted SSE (ties to the lower index),   */
+/* taken in ascending index order.                                              */
+static void seed_lbg(const uint32_t *keys, const uint32_t *w, int64_t n, int K, double lbg_eps, double conv_eps,
+                     int max_iter, double *c)
+{
+    uint8_t *labels = (uint8_t *)malloc((size_t)n);
+    int64_t *sums = (int64_t *)calloc((size_t)K * 4, sizeof(int64_t));
+    int64_t W = 0, s[3] = {0, 0, 0};
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t x[3];
+        key_rgb(keys[i], &x[0], &x[1], &x[2]);
+        W += (int64_t)w[i];
+        for (int ch = 0; ch < 3; ++ch) s[ch] += (int64_t)w[i] * x[ch];
+    }
+    for (int ch = 0; ch < 3; ++ch) c[ch] = (double)s[ch] / (double)W;
+    int m = 1;
+    while (m < K) {
+        int split = (2 * m <= K) ? m : K - m;
+        int *chosen = (int *)malloc(sizeof(int) * (size_t)m);
+        if (split == m) {
+            for (int j = 0; j < m; ++j) chosen[j] = 1;
+        } else {
+            /* rank clusters of the current assignment by exact SSE */
+            __int128 *num = (__int128 *)calloc((size_t)m, sizeof(__int128));
+            int64_t *cw = (int64_t *)calloc((size_t)m, sizeof(int64_t));
+            int64_t *cs = (int64_t *)calloc((size_t)m * 3, sizeof(int64_t));
+            __int128 *sq = (__int128 *)calloc((size_t)m, sizeof(__int128));
+            for (int64_t i = 0; i < n; ++i) {
+                int64_t x[3];
+                key_rgb(keys[i], &x[0], &x[1], &x[2]);
+                int k = labels[i];
+                cw[k] += (int64_t)w[i];
+                for (int ch = 0; ch < 3; ++ch) cs[3 * k + ch] += (int64_t)w[i] * x[ch];
+                sq[k] += (__int128)w[i] * (x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+            }
+            for (int k = 0; k < m; ++k) {
+                __int128 s2 = 0;
+                for (int ch = 0; ch < 3; ++ch) s2 += (__int128)cs[3 * k + ch] * cs[3 * k + ch];
+                num[k] = (__int128)cw[k] * sq[k] - s2;
+            }
+            for (int j = 0; j < m; ++j) chosen[j] = 0;
+            for (int t = 0; t < split; ++t) {
+                int arg = -1;
+                for (int k = 0; k < m; ++k) {
+                    if (chosen[k]) continue;
+                    if (arg < 0 || sse_greater(num[k], cw[k], num[arg], cw[arg])) arg = k;
+                }
+                chosen[arg] = 1;
+            }
+            free(num);
+            free(cw);
+            free(cs);
+            free(sq);
+        }
+        int q = 0;
+        for (int j = 0; j < m; ++j) {
+            if (!chosen[j]) continue;
+            for (int ch = 0; ch < 3; ++ch) {
+                double base = c[3 * j + ch];
+                c[3 * (m + q) + ch] = base + lbg_eps;
+                c[3 * j + ch] = base - lbg_eps;
+            }
+            ++q;
+        }
+        free(chosen);
+        m += split;
+        or_lloyd(keys, w, n, m, c, conv_eps, max_iter, labels, NULL, NULL, sums);
+    }
+    free(labels);
+    free(sums);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Entry point for seeding.  K_eff = min(K, N'); for K >= N' the centres are   */
+/* the unique colours in key order, padded with copies of the last one.        */
+/* Returns K_eff, or -1 for an unknown scheme.                                 */
+/* ------------------------------------------------------------------------- */
+OR_API int or_seed(const uint32_t *keys, const uint32_t *w, int64_t n, int K, int scheme, uint64_t seed,
+                   double lbg_eps, double conv_eps, int max_iter, double *c)
+{
+    if (n <= 0 || K <= 0) return -1;
+    if (K >= n) {
+        for (int64_t i = 0; i < n; ++i) centre_from_key(c + 3 * i, keys[i]);
+        for (int k = (int)n; k < K; ++k) memcpy(c + 3 * k, c + 3 * (n - 1), 3 * sizeof(double));
+        return (int)n;
+    }
+    switch (scheme) {
+    case OR_FGY: seed_fgy(keys, n, K, seed, c); break;
+    case OR_LBG: seed_lbg(keys, w, n, K, lbg_eps, conv_eps, max_iter, c); break;
+    case OR_MMX: seed_mmx(keys, n, K, seed, c); break;
+    case OR_DEN: seed_den(keys, w, n, K, seed, c); break;
+    case OR_VAR: seed_var(keys, w, n, K, c); break;
+    case OR_SFF: seed_sff(keys, n, K, seed, c); break;
+    case OR_KPP: seed_kpp(keys, w, n, K, seed, c); break;
+    default: return -1;
+    }
+    return K;
+}
