@@ -1,0 +1,403 @@
+#!/usr/bin/env python
+"""Benchmark: exact k-means colour quantization (Weighted Sort-Means) on GB300.
+
+One step = the whole hot path on one synthetic 512 x 512 RGB8 image already in
+HBM: kq_histogram -> kq_seed (k-means++) -> kq_lloyd (K = 256, eps 1e-4, at most
+100 passes) -> kq_map.  Every step is timed with CUDA events on the launching
+stream; between steps a 256 MiB buffer is written to flush the 129 MB L2 (not
+timed).  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank quantizes its own image (independent
+replicas, no data exchange); value = pixels of all ranks / max step time.
+--impl reference times the FP64 CPU oracle on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "paper_512"
+K_DEFAULT = 256
+SCHEME = "KPP"
+SEED = 1101
+FLOP_PER_DIST = 8          # 3 subtractions, 1 multiply, 2 fused multiply-adds
+FP32_LANES_PER_SM = 128
+METRIC = "Mpix/s end-to-end"
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=300)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="kq", choices=["kq", "reference"])
+    p.add_argument("--workload", default=WORKLOAD)
+    p.add_argument("--K", type=int, default=K_DEFAULT)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args(argv)
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def reduce_max(value: float, world: int) -> float:
+    """Max over ranks (host timing plumbing; no data-path collective)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int) -> None:
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def aggregate(pixels_per_rank: int, world: int, ms_per_step_max: float) -> float:
+    """Whole-job Mpix/s: pixels processed by all ranks per step / slowest rank's step time."""
+    return pixels_per_rank * world / (ms_per_step_max * 1e-3) / 1e6
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms while running."""
+
+    FIELDS = ["clocks.sm", "clocks.max.sm", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) != len(self.FIELDS):
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[2:]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def cpu_baseline(img, K: int, eps: float, max_iter: int, budget_s: float = 12.0) -> dict:
+    """The FP64 oracle, as it stands, on the host cores: whole quantizations of
+    the same image until `budget_s` of CPU work (at least one)."""
+    import oracle
+
+    n = img.size // 3
+    times = []
+    t_total = 0.0
+    while not times or t_total < budget_s:
+        t0 = time.perf_counter()
+        oracle.quantize(img, K, SCHEME, SEED, eps, max_iter)
+        dt = time.perf_counter() - t0
+        times.append(dt)
+        t_total += dt
+        if len(times) >= 20:
+            break
+    mean = sum(times) / len(times)
+    return {"value": n / mean / 1e6, "unit": "Mpix/s", "cores": 1, "kind": "oracle",
+            "sample": "%d whole quantization(s) of the %dx%d image (K=%d, %s, eps=%g, <=%d passes), %.1f s"
+                      % (len(times), img.shape[0], img.shape[1], K, SCHEME, eps, max_iter, t_total),
+            "cpu": cpu_model(), "nproc": os.cpu_count()}
+
+
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                low = line.lower()
+                if low.startswith("model name") or low.startswith("cpu part") or low.startswith("hardware"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def workload_config(wl, img, K, n_unique=None, iters=None) -> dict:
+    cfg = {"workload": "%s: one %dx%d synthetic RGB8 image (%d regions, noise %g), K=%d, %s seeds, eps=%g, "
+                       "<=%d passes" % (wl.name, wl.height, wl.width, wl.regions, wl.sigma_n, K, SCHEME, wl.eps,
+                                        wl.max_iter),
+           "n_pixels": int(img.size // 3), "K": K, "l2": "flushed between steps (256 MiB write, untimed)",
+           "parallelism": "replicas (one image per GPU)"}
+    if n_unique is not None:
+        cfg["n_unique"] = int(n_unique)
+    if iters is not None:
+        cfg["lloyd_passes"] = int(iters)
+    return cfg
+
+
+def run_reference(args, rank, world) -> None:
+    """The reference arm: the FP64 CPU oracle on the same workload."""
+    if rank != 0:
+        return
+    import oracle  # noqa: F401
+    from paper_1101_0395_gb300 import synth
+
+    wl = synth.WORKLOADS[args.workload]
+    img = wl.make(0)
+    K = args.K
+    n = img.size // 3
+    import oracle as orc
+
+    for _ in range(max(0, args.warmup)):
+        orc.quantize(img, K, SCHEME, SEED, wl.eps, wl.max_iter)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        out = orc.quantize(img, K, SCHEME, SEED, wl.eps, wl.max_iter)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(times) / len(times)
+    value = n / (ms * 1e-3) / 1e6
+    line = {"metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": workload_config(wl, img, K, out["keys"].size, out["iters"]),
+            "cpu_baseline": {"value": value, "unit": "Mpix/s", "kind": "oracle", "cores": 1,
+                             "sample": "whole quantizations of the %dx%d image, one per step" % img.shape[:2]},
+            "e2e": {"value": value, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args, rank, world, local) -> None:
+    import numpy as np
+    import torch
+
+    from paper_1101_0395_gb300 import kq, synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = synth.WORKLOADS[args.workload]
+    K = args.K
+    img = wl.make(rank)
+    n = img.size // 3
+    q = kq.Quantizer(n, device=dev)
+    rgb = torch.from_numpy(img.reshape(-1)).to(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def stage_calls(src, quant):
+        kq.kq_histogram(src, quant.keys, quant.weights, quant.n_unique, quant.ws)
+        yield
+        c = quant.centers[:3 * K]
+        kq.kq_seed(quant.keys, quant.weights, quant.n_unique, K, SCHEME, SEED, c, quant.ws, conv_eps=wl.eps,
+                   max_iter=wl.max_iter)
+        yield
+        pal = quant.palette[:3 * K]
+        kq.kq_lloyd(quant.keys, quant.weights, quant.n_unique, K, c, wl.eps, wl.max_iter, quant.labels, pal,
+                    quant.ws, stats=quant.stats)
+        yield
+        kq.kq_map(src, quant.keys, quant.weights, quant.n_unique, pal, K, quant.idx[:n], quant.ws,
+                  sse_num=quant.sse_num)
+        yield
+
+    launches_per_step = (kq.launches("kq_histogram", n) + kq.launches("kq_seed", n, SCHEME, K)
+                         + kq.launches("kq_lloyd") + kq.launches("kq_map", n))
+
+    for _ in range(max(3, args.warmup)):
+        for _ in stage_calls(rgb, q):
+            pass
+    torch.cuda.synchronize()
+    st = kq.parse_stats(q.stats)
+    n_unique = int(q.n_unique.item())
+    status = kq.kq_status_read(q.ws)
+    if status != kq.KQ_OK:
+        raise RuntimeError("device status after warm-up: %s" % kq.strerror(status))
+
+    steps = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(steps)]
+    props = torch.cuda.get_device_properties(dev)
+    gpu_id = "GPU-%s" % props.uuid if getattr(props, "uuid", None) else str(local)
+    clocks = ClockSampler(gpu_id)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for s in range(steps):
+        flush.fill_(s & 255)
+        e = ev[s]
+        e[0].record(stream)
+        for j, _ in enumerate(stage_calls(rgb, q)):
+            e[j + 1].record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    step_ms = [e[0].elapsed_time(e[4]) for e in ev]
+    stage_ms = [[e[j].elapsed_time(e[j + 1]) for e in ev] for j in range(4)]
+    ms_local = sum(step_ms) / steps
+    ms_max = reduce_max(ms_local, world)
+    value = aggregate(n, world, ms_max)
+    stage_mean = [sum(x) / steps for x in stage_ms]
+
+    # ---- end to end through the public API with host buffers
+    h_rgb = torch.from_numpy(img.reshape(-1).copy()).pin_memory()
+    h_idx = torch.empty(n, dtype=torch.uint8).pin_memory()
+    h_pal = torch.empty(3 * K, dtype=torch.uint8).pin_memory()
+    h_stats = torch.empty(64, dtype=torch.uint8).pin_memory()
+    d_rgb = torch.empty(3 * n, dtype=torch.uint8, device=dev)
+    e2e_steps = max(10, min(steps, 100))
+    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(e2e_steps)]
+    for s in range(e2e_steps + 3):
+        if s >= 3:
+            flush.fill_(s & 255)
+            e2e_ev[s - 3][0].record(stream)
+        d_rgb.copy_(h_rgb, non_blocking=True)
+        res = q.quantize(d_rgb, K, SCHEME, SEED, wl.eps, wl.max_iter)
+        h_idx.copy_(res.idx, non_blocking=True)
+        h_pal.copy_(res.palette.view(-1), non_blocking=True)
+        h_stats.copy_(res.stats, non_blocking=True)
+        if s >= 3:
+            e2e_ev[s - 3][1].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = reduce_max(sum(a.elapsed_time(b) for a, b in e2e_ev) / e2e_steps, world)
+    if not np.array_equal(h_idx.numpy(), q.idx[:n].cpu().numpy()):
+        raise RuntimeError("end-to-end result differs from the device-resident run")
+
+    # ---- roofline of the dominant kernel
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz") or 2070.0)
+    fp32_peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
+    hbm_peak = float(peaks.get("hbm_gbs") or 6800.0)
+    names = ["kq_histogram", "kq_seed", "kq_lloyd", "kq_map"]
+    dom = max(range(4), key=lambda j: stage_mean[j])
+    lloyd_s = stage_mean[2] * 1e-3
+    gdist_actual = st["ndc"] / lloyd_s / 1e9
+    gdist_dense = n_unique * K * st["iters"] / lloyd_s / 1e9
+    if dom == 2:
+        achieved = st["ndc"] * FLOP_PER_DIST / lloyd_s / 1e12
+        roof = {"kernel": "lloyd_kernel (kq_lloyd: one persistent launch, all passes)", "bound": "alu",
+                "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                "traffic": None,
+                "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 FLOP x %.0f MHz (max SM clock, measured)"
+                               % (props.multi_processor_count, sm_max),
+                "algorithmic": "%d FLOP per distance x NDC %d" % (FLOP_PER_DIST, st["ndc"])}
+    elif dom == 1:
+        # seeding: each of K rounds reads key, weight and D^2 and writes D^2 per unique colour
+        byts = 16.0 * n_unique * K
+        achieved = byts / (stage_mean[1] * 1e-3) / 1e9
+        roof = {"kernel": "seed_far (kq_seed, k-means++)", "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
+                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None, "peak_source": "MEASURED_PEAKS hbm_gbs",
+                "algorithmic": "16 B per unique colour per round x %d rounds" % K}
+    else:
+        byts = (3.0 * n + 8.0 * n_unique) if dom == 0 else (4.0 * n + 8.0 * n_unique)
+        achieved = byts / (stage_mean[dom] * 1e-3) / 1e9
+        roof = {"kernel": names[dom], "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None, "peak_source": "MEASURED_PEAKS hbm_gbs",
+                "algorithmic": "pixels 3 B in (+1 B out) + 8 B per unique colour"}
+
+    line = {"metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(wl, img, K, n_unique, st["iters"]),
+            "clocks": {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+            "e2e": {"value": aggregate(n, world, e2e_ms), "unit": "Mpix/s", "h2d_bytes_per_step": 3 * n,
+                    "d2h_bytes_per_step": n + 3 * K + 64},
+            "gpu_launches": launches_per_step * steps,
+            "roofline": roof,
+            "gdist_evals_per_s": {"actual": gdist_actual, "dense_equivalent": gdist_dense, "unit": "G/s",
+                                  "ndc_per_colour_per_pass": st["ndc"] / max(1, n_unique * st["iters"])},
+            "stages_ms": dict(zip(names, stage_mean)),
+            "wall_s_timed_region": wall, "clock_samples": clk["samples"]}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(img, K, wl.eps, wl.max_iter)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main(argv=None) -> None:
+    args = parse_args(argv)
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        backend = "nccl" if args.impl == "kq" else "gloo"
+        if backend == "nccl":
+            import torch
+
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    try:
+        if args.impl == "reference":
+            run_reference(args, rank, world)
+        else:
+            run_gpu(args, rank, world, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,196 @@
+/*
+ * kq.h -- C ABI of the GB300 exact k-means colour quantizer (Weighted Sort-Means,
+ * M. E. Celebi, "Improving the Performance of K-Means for Color Quantization",
+ * Image and Vision Computing 29(4), 2011; arXiv:1101.0395).
+ *
+ * The four steps of the method, each one call:
+ *   kq_histogram  unique colours with integer weights          (Section 2.2, items 1-2)
+ *   kq_seed       initial centres by a generic scheme           (Section 2.3)
+ *   kq_lloyd      weighted Lloyd with sort-means pruning        (Section 2.2 item 3, Algorithm 2;
+ *                 stopping test of Section 3.3)
+ *   kq_map        nearest palette colour per pixel, and SSE     (Section 1; MSE of Section 3.1, Eq. 2)
+ *
+ * Conventions for every entry point:
+ *  - Pointers are DEVICE pointers unless the name starts with h_.  The caller
+ *    allocates and owns every buffer, including the workspace `ws`; no entry
+ *    point allocates device memory.
+ *  - Every call is asynchronous on `stream` (a cudaStream_t; NULL is the legacy
+ *    default stream) and returns after enqueueing its kernels.
+ *  - The return value is a kq_status.  Invalid arguments (a null pointer, K
+ *    outside 1..256, a workspace that is too small, a misaligned workspace)
+ *    return KQ_EINVAL synchronously and enqueue nothing.  A failed kernel
+ *    launch returns KQ_ECUDA.
+ *  - Conditions found on the device (more unique colours than `capacity`, a
+ *    barrier wait that timed out) are written to a status word inside `ws`.
+ *    kq_status_read() returns it.  The first error is kept until
+ *    kq_status_clear().
+ *  - Colours are 24-bit keys (R << 16) | (G << 8) | B.  Pixels are packed
+ *    HWC RGB8, 3 bytes per pixel, in any alignment.
+ *  - Ties between equally near centres or palette entries go to the lowest index.
+ *  - The workspace must be zero-filled once (kq_workspace_init()) before its
+ *    first use; the library keeps its table regions zeroed between calls.
+ *    Calls that share one workspace must be ordered on the GPU (one stream,
+ *    or events); calls on separate workspaces are independent.
+ *  - K is at most 256, so a palette index fits in a uint8_t.
+ */
+#ifndef KQ_H
+#define KQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define KQ_API __attribute__((visibility("default")))
+#else
+#define KQ_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *kq_stream_t; /* the same type as cudaStream_t */
+
+typedef enum {
+    KQ_OK = 0,
+    KQ_EINVAL = -1,    /* invalid argument (synchronous) */
+    KQ_ECAPACITY = -2, /* more unique colours than the caller's capacity (device status) */
+    KQ_ECUDA = -3,     /* a CUDA runtime call failed */
+    KQ_ETIMEOUT = -4,  /* a device-side wait passed its time limit (device status) */
+    KQ_ENOMEM = -5     /* the workspace is too small for the request */
+} kq_status;
+
+/* Initialization schemes (Section 2.3).  KQ_INIT_USER: the caller's centres. */
+typedef enum {
+    KQ_INIT_FGY = 0, /* Forgy: K distinct unique colours, uniformly */
+    KQ_INIT_LBG = 1, /* splitting (Linde-Buzo-Gray) from the centroid */
+    KQ_INIT_MMX = 2, /* minmax (farthest first) */
+    KQ_INIT_DEN = 3, /* density-based: 64 uniform cells, seats by pixel count */
+    KQ_INIT_VAR = 4, /* maximum variance: medians of K groups on the widest channel */
+    KQ_INIT_SFF = 5, /* subset farthest first on ceil(2 K ln K) random colours */
+    KQ_INIT_KPP = 6, /* k-means++ (D^2 sampling, pixel-weighted) */
+    KQ_INIT_USER = 7
+} kq_init;
+
+/* Parameters the paper leaves open; pass NULL for the defaults in brackets. */
+typedef struct kq_seed_params {
+    double lbg_eps;    /* LBG perturbation per channel, 0-255 units [1.0] */
+    double conv_eps;   /* LBG refinement: relative SSE threshold [1e-4] */
+    int32_t max_iter;  /* LBG refinement: iteration limit [100] */
+    int32_t reserved;  /* must be 0 */
+} kq_seed_params;
+
+/* Device-side statistics written by kq_lloyd (caller-owned device memory). */
+typedef struct kq_lloyd_stats {
+    int32_t iters;     /* assignment+update passes run */
+    int32_t converged; /* 1 when the relative SSE test of Section 3.3 fired */
+    int32_t k_eff;     /* min(K, N') */
+    int32_t status;    /* KQ_OK, or the device error that stopped the run */
+    int64_t ndc;       /* distance calculations, the paper's NDC count, summed over iterations */
+    double sse;        /* pixel-weighted SSE of the last assignment (Eq. 1) */
+    double sse_prev;   /* SSE of the assignment before it (0 after one pass) */
+} kq_lloyd_stats;
+
+/* kq_lloyd flags */
+#define KQ_LLOYD_LABELS_IN 1u /* `labels` holds a previous assignment: prune from the first pass */
+#define KQ_LLOYD_DENSE 2u     /* full search of all K centres in every pass (no pruning) */
+
+/*
+ * Bytes of workspace needed for images of up to `max_pixels` pixels and
+ * palettes of up to `max_K` colours (1..256).  Returns 0 for invalid sizes.
+ * The workspace must be 256-byte aligned (any cudaMalloc/torch allocation is).
+ */
+KQ_API size_t kq_workspace_size(int64_t max_pixels, int32_t max_K);
+
+/* Zero-fills the workspace on `stream` (once, before its first use). */
+KQ_API int kq_workspace_init(void *ws, size_t ws_bytes, kq_stream_t stream);
+
+/*
+ * Unique colours and their pixel counts (Section 2.2: sampling of the pixels
+ * with unique colours, each weighted by its frequency -- a colour histogram).
+ *   rgb        n_pixels x 3 bytes, packed HWC.
+ *   keys       out: N' unique colours in ascending key order (capacity entries).
+ *   weights    out: pixel count of each unique colour (integer; the paper's
+ *              weights are these divided by n_pixels).
+ *   capacity   entries available in keys and weights.
+ *   n_unique   out (device int32): min(N', capacity).  When N' > capacity the
+ *              first `capacity` colours are written and the device status
+ *              becomes KQ_ECAPACITY.
+ * n_pixels may be 0 (then N' = 0).  Bit-exact: the result is unique.
+ */
+KQ_API int kq_histogram(const uint8_t *rgb, int64_t n_pixels, uint32_t *keys, uint32_t *weights, int32_t capacity,
+                 int32_t *n_unique, void *ws, size_t ws_bytes, kq_stream_t stream);
+
+/*
+ * Initial centres by a generic scheme of Section 2.3.
+ *   keys, weights, n_unique   the output of kq_histogram.
+ *   K          palette size, 1..256.  When K >= N' the centres are the N'
+ *              unique colours in key order, padded with copies of the last.
+ *   scheme     a kq_init value other than KQ_INIT_USER.
+ *   seed       random seed.  Draw number i of stream s is output
+ *              s * 2^32 + i + 1 of SplitMix64 seeded with `seed`; an integer
+ *              in [0, m) is the high 64 bits of that output times m.
+ *   params     NULL for the defaults (LBG only).
+ *   centers    out: K x 3 doubles (FP64; integer-valued except for LBG).
+ * Every scheme except LBG is bit-exact (integer arithmetic throughout).
+ */
+KQ_API int kq_seed(const uint32_t *keys, const uint32_t *weights, const int32_t *n_unique, int32_t K, int32_t scheme,
+            uint64_t seed, const kq_seed_params *params, double *centers, void *ws, size_t ws_bytes,
+            kq_stream_t stream);
+
+/*
+ * Weighted Sort-Means (Algorithm 2): repeated passes of
+ *   assignment -- nearest centre per unique colour, scanning the centres in
+ *                 increasing distance from the previous centre p and stopping
+ *                 once d(c_p, c_t) rules out any nearer centre (Section 2.2,
+ *                 item 3); distances in FP32; the labels equal those of a full
+ *                 FP32 search (lowest index on ties);
+ *   update     -- weighted means from exact int64 sums, divided in FP64; an
+ *                 empty cluster keeps its centre;
+ *   stop test  -- after pass i, stop when SSE_i == 0 or, for i > 1,
+ *                 (SSE_{i-1} - SSE_i) / SSE_i <= eps (Section 3.3); eps < 0
+ *                 runs exactly max_iter passes (the protocol of Section 3.2).
+ *   centers    in: K x 3 FP64 seeds; out: the final centres.
+ *   max_iter   pass limit, >= 1.
+ *   flags      KQ_LLOYD_LABELS_IN, KQ_LLOYD_DENSE.
+ *   labels     N' bytes: in (with KQ_LLOYD_LABELS_IN) and out (last assignment).
+ *   palette    out: K x 3 bytes, each centre rounded half-up: floor((2S+W)/(2W))
+ *              per channel from the exact sums; an empty cluster rounds its
+ *              held centre (floor(c + 0.5), clamped to 0..255).
+ *   stats      out (device): see kq_lloyd_stats.  May be NULL.
+ *   sse_hist   out (device, nullable): SSE of each pass, max_iter doubles.
+ * The whole loop runs on the device as one cooperative launch; the host never
+ * waits between passes.
+ */
+KQ_API int kq_lloyd(const uint32_t *keys, const uint32_t *weights, const int32_t *n_unique, int32_t K, double *centers,
+             double eps, int32_t max_iter, uint32_t flags, uint8_t *labels, uint8_t *palette, kq_lloyd_stats *stats,
+             double *sse_hist, void *ws, size_t ws_bytes, kq_stream_t stream);
+
+/*
+ * Pixel mapping (Section 1; Section 2.1 notes that k-means maps by a full
+ * palette search): idx[i] = argmin_k |rgb_i - palette_k|^2 in exact integer
+ * arithmetic, lowest index on ties.
+ *   keys, weights, n_unique   kq_histogram's output for THIS image (each unique
+ *              colour is matched once, then every pixel looks its colour up).
+ *   palette    K x 3 bytes.   idx   out: n_pixels bytes.
+ *   sse_num    out (device int64, nullable): sum over pixels of the squared
+ *              error, the numerator of the MSE of Section 3.1 (Eq. 2).
+ */
+KQ_API int kq_map(const uint8_t *rgb, int64_t n_pixels, const uint32_t *keys, const uint32_t *weights,
+           const int32_t *n_unique, const uint8_t *palette, int32_t K, uint8_t *idx, int64_t *sse_num, void *ws,
+           size_t ws_bytes, kq_stream_t stream);
+
+/* Device status word of `ws` copied to *h_status (synchronizes `stream`). */
+KQ_API int kq_status_read(const void *ws, int32_t *h_status, kq_stream_t stream);
+
+/* Resets the device status word of `ws` to KQ_OK (asynchronous). */
+KQ_API int kq_status_clear(void *ws, kq_stream_t stream);
+
+/* Static description of a status code. */
+KQ_API const char *kq_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KQ_H */

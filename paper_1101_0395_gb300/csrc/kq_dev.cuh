@@ -1,0 +1,317 @@
+// kq_dev.cuh -- internal declarations shared by the CUDA translation units of libkq.
+//
+// Workspace layout, the device status word, the bounded grid barrier used by the
+// cooperative (persistent) kernels, the counter-based random numbers and the one
+// FP32 distance formula that every assignment path uses.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/kq.h"
+
+namespace kq {
+
+// ---------------------------------------------------------------- constants
+constexpr int kMaxK = 256;                 // palette indices are uint8_t
+constexpr int kKeyBits = 24;               // (R << 16) | (G << 8) | B
+constexpr int64_t kKeySpace = int64_t(1) << kKeyBits;
+constexpr int kBitWords = 1 << (kKeyBits - 5);   // presence bitmap, one bit per colour
+constexpr int kHistChunkWords = 2048;            // bitmap words per compaction block
+constexpr int kHistChunks = kBitWords / kHistChunkWords;  // 256
+constexpr int kMaxGrid = 4096;             // upper bound on persistent grid sizes
+constexpr int kSeedChunks = 512;           // chunks of the unique list for VAR / DEN lookups
+constexpr int kDenCells = 64;              // 4 levels per channel
+constexpr uint64_t kWaitNs = 4000000000ull;  // device-side wait limit (4 s)
+
+// ---------------------------------------------------------------- control block
+// Lives at the start of the workspace.  Fields touched by spinning blocks sit on
+// their own 128-byte lines.
+struct Ctl {
+    int32_t status;            // first device-side error (kq_status), 0 = OK
+    uint32_t abort;            // set when a wait timed out: every wait then gives up
+    int64_t n_unique_true;     // N' before clamping to the caller's capacity
+    unsigned long long ndc;    // distance calculations of the current kq_lloyd call
+    uint32_t pad0[26];
+    uint32_t bar_count;        // grid barrier: arrivals in this generation
+    uint32_t pad1[31];
+    uint32_t bar_gen;          // grid barrier: generation number
+    uint32_t pad2[31];
+    // seeding scratch scalars
+    unsigned long long var_w;  // sum of weights
+    unsigned long long var_s1[3];
+    unsigned long long var_s2[3];
+    uint32_t pad3[18];
+};
+static_assert(sizeof(Ctl) <= 4096, "control block must fit its region");
+
+// ---------------------------------------------------------------- workspace layout
+struct Layout {
+    size_t ctl, hist_cnt, hist_bits, hist_chunk, lut;
+    size_t l_sums, l_sse, l_rows;
+    size_t s_d2, s_part, s_slot, s_chunk, s_gcnt, s_misc, s_labels, s_centers;
+    size_t total;
+    int64_t max_unique;
+};
+
+__host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Fixed-size regions first, then the two that grow with the number of unique
+// colours (8 + 1 bytes per colour), so that the layout of a workspace can be
+// recovered from its size alone.
+__host__ __device__ inline Layout layout_for(int64_t max_unique)
+{
+    Layout L{};
+    int64_t mu = max_unique < kKeySpace ? max_unique : kKeySpace;
+    if (mu < 1) mu = 1;
+    L.max_unique = mu;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + bytes, 256); return at; };
+    L.ctl = take(4096);
+    L.hist_cnt = take(sizeof(uint32_t) * (size_t)kKeySpace);
+    L.hist_bits = take(sizeof(uint32_t) * (size_t)kBitWords);
+    L.hist_chunk = take(sizeof(uint32_t) * (size_t)kHistChunks);
+    L.lut = take((size_t)kKeySpace);
+    L.l_sums = take(sizeof(unsigned long long) * 3 * kMaxK * 4);
+    L.l_sse = take(sizeof(double) * 2 * kMaxGrid);
+    L.l_rows = take(sizeof(uint32_t) * kMaxK * kMaxK);
+    L.s_part = take(sizeof(unsigned long long) * 2 * kMaxGrid);
+    L.s_slot = take(sizeof(unsigned long long) * kMaxK);
+    L.s_chunk = take(sizeof(uint32_t) * (size_t)kSeedChunks * 3 * 256);
+    L.s_gcnt = take(sizeof(uint32_t) * 3 * 256 + sizeof(unsigned long long) * kDenCells * 2);
+    L.s_misc = take(65536);
+    L.s_centers = take(sizeof(double) * kMaxK * 3);
+    L.s_d2 = take(2 * sizeof(uint32_t) * (size_t)mu);
+    L.s_labels = take((size_t)mu);
+    L.total = o;
+    return L;
+}
+
+// Largest layout that fits in `bytes` (max_unique = 0 when even one colour does not fit).
+inline Layout layout_from_bytes(size_t bytes)
+{
+    Layout base = layout_for(1);
+    if (bytes < base.total) {
+        Layout none{};
+        none.max_unique = 0;
+        return none;
+    }
+    int64_t mu = (int64_t)((bytes - base.s_d2) / 9);
+    if (mu > kKeySpace) mu = kKeySpace;
+    if (mu < 1) mu = 1;
+    Layout L = layout_for(mu);
+    while (L.total > bytes && mu > 1) {  // alignment padding: step down until it fits
+        mu = mu > 256 ? mu - 256 : 1;
+        L = layout_for(mu);
+    }
+    return L;
+}
+
+template <typename T>
+__host__ __device__ inline T *at(void *ws, size_t off) { return reinterpret_cast<T *>(static_cast<char *>(ws) + off); }
+
+// ---------------------------------------------------------------- device helpers
+__device__ __forceinline__ void fail(Ctl *ctl, int code) { atomicCAS(&ctl->status, 0, code); }
+
+__device__ __forceinline__ uint64_t globaltimer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Barrier over the first `nblocks` blocks of a cooperative launch.  Every wait is
+// bounded: after kWaitNs, or when another block has given up, it records
+// KQ_ETIMEOUT, raises `abort` and returns false; the caller then returns.
+__device__ __forceinline__ bool grid_sync(Ctl *ctl, unsigned nblocks)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile uint32_t *genp = &ctl->bar_gen;
+        volatile uint32_t *abortp = &ctl->abort;
+        uint32_t gen = *genp;
+        __threadfence();
+        if (*abortp) {
+            ok = 0;
+        } else {
+            uint32_t arrived = atomicAdd(&ctl->bar_count, 1u);
+            if (arrived == nblocks - 1) {
+                atomicExch(&ctl->bar_count, 0u);
+                __threadfence();
+                atomicAdd(&ctl->bar_gen, 1u);
+            } else {
+                uint64_t t0 = globaltimer_ns();
+                while (*genp == gen) {
+                    if (*abortp) { ok = 0; break; }
+                    if (globaltimer_ns() - t0 > kWaitNs) {
+                        fail(ctl, KQ_ETIMEOUT);
+                        atomicExch(&ctl->abort, 1u);
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(40);
+                }
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// SplitMix64 (Steele, Lea and Flood, OOPSLA 2014): draw `ctr` of stream `stream`
+// is output number stream * 2^32 + ctr + 1 of the generator seeded with `seed`.
+__host__ __device__ __forceinline__ uint64_t rand64(uint64_t seed, uint32_t stream, uint32_t ctr)
+{
+    uint64_t n = ((uint64_t)stream << 32) + (uint64_t)ctr + 1ull;
+    uint64_t z = seed + n * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Integer in [0, m): the high half of the 128-bit product.
+__device__ __forceinline__ uint64_t below(uint64_t u, uint64_t m) { return __umul64hi(u, m); }
+
+__device__ __forceinline__ uint32_t key_r(uint32_t k) { return k >> 16; }
+__device__ __forceinline__ uint32_t key_g(uint32_t k) { return (k >> 8) & 255u; }
+__device__ __forceinline__ uint32_t key_b(uint32_t k) { return k & 255u; }
+
+// Squared distance in FP32: differences first, then squares summed by two fused
+// multiply-adds, every operation rounded to nearest.  The pruned scan, the full
+// search and the centre-to-centre table all call this one function, so equal
+// inputs give bitwise-equal distances everywhere.
+__device__ __forceinline__ float dist3(float x, float y, float z, float cx, float cy, float cz)
+{
+    float dx = __fsub_rn(x, cx), dy = __fsub_rn(y, cy), dz = __fsub_rn(z, cz);
+    return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+}
+
+// Exact integer squared distance between two colours.
+__device__ __forceinline__ uint32_t key_dist2(uint32_t a, uint32_t b)
+{
+    int dr = (int)key_r(a) - (int)key_r(b), dg = (int)key_g(a) - (int)key_g(b), db = (int)key_b(a) - (int)key_b(b);
+    return (uint32_t)(dr * dr + dg * dg + db * db);
+}
+
+// ---------------------------------------------------------------- block reductions
+template <int BLOCK>
+__device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v, unsigned long long *scratch)
+{
+    for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) scratch[warp] = v;
+    __syncthreads();
+    unsigned long long t = 0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < BLOCK / 32; ++i) t += scratch[i];
+    return t;  // valid in thread 0
+}
+
+// Fixed-order FP64 block sum: a fixed shuffle tree per warp, then warp results
+// in warp order.  The same inputs in the same threads give the same bits.
+template <int BLOCK>
+__device__ __forceinline__ double block_sum_f64(double v, double *scratch)
+{
+    for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) scratch[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < BLOCK / 32; ++i) t += scratch[i];
+    return t;  // valid in thread 0
+}
+
+// Block-wide exclusive scan of 32-bit counts; returns this thread's exclusive
+// prefix and writes the block total to *total (all threads).
+template <int BLOCK>
+__device__ __forceinline__ uint32_t block_excl_scan_u32(uint32_t v, uint32_t *scratch, uint32_t *total)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    __syncthreads();
+    if (lane == 31) scratch[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t s = lane < BLOCK / 32 ? scratch[lane] : 0u;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < BLOCK / 32) scratch[lane] = s;
+    }
+    __syncthreads();
+    uint32_t before = warp ? scratch[warp - 1] : 0u;
+    *total = scratch[BLOCK / 32 - 1];
+    return before + x - v;
+}
+
+template <int BLOCK>
+__device__ __forceinline__ unsigned long long block_excl_scan_u64(unsigned long long v, unsigned long long *scratch,
+                                                                  unsigned long long *total)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned long long x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    __syncthreads();
+    if (lane == 31) scratch[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned long long s = lane < BLOCK / 32 ? scratch[lane] : 0ull;
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned long long y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < BLOCK / 32) scratch[lane] = s;
+    }
+    __syncthreads();
+    unsigned long long before = warp ? scratch[warp - 1] : 0ull;
+    *total = scratch[BLOCK / 32 - 1];
+    return before + x - v;
+}
+
+// Contiguous slice [lo, hi) of n items for block b of g.
+__device__ __forceinline__ void slice_of(int64_t n, int b, int g, int64_t *lo, int64_t *hi)
+{
+    int64_t per = (n + g - 1) / g;
+    int64_t a = (int64_t)b * per;
+    *lo = a < n ? a : n;
+    int64_t e = a + per;
+    *hi = e < n ? e : n;
+}
+
+}  // namespace kq
+
+// ---------------------------------------------------------------- host-side launchers
+namespace kq {
+struct DeviceInfo {
+    int device;
+    int sms;
+};
+DeviceInfo device_info();
+int max_coresident(const void *kernel, int block, size_t smem);
+
+int launch_histogram(const uint8_t *rgb, int64_t n, uint32_t *keys, uint32_t *weights, int32_t cap, int32_t *n_unique,
+                     void *ws, const Layout &L, cudaStream_t s);
+int launch_lloyd(const uint32_t *keys, const uint32_t *w, const int32_t *n_unique, int K, double *centers, double eps,
+                 int max_iter, uint32_t flags, uint8_t *labels, uint8_t *palette, kq_lloyd_stats *stats,
+                 double *sse_hist, void *ws, const Layout &L, cudaStream_t s, int skip_if_n_le);
+int launch_seed(const uint32_t *keys, const uint32_t *w, const int32_t *n_unique, int K, int scheme, uint64_t seed,
+                const kq_seed_params &p, double *centers, void *ws, const Layout &L, cudaStream_t s);
+int launch_map(const uint8_t *rgb, int64_t n, const uint32_t *keys, const uint32_t *w, const int32_t *n_unique,
+               const uint8_t *palette, int K, uint8_t *idx, int64_t *sse_num, void *ws, const Layout &L,
+               cudaStream_t s);
+}  // namespace kq

@@ -1,0 +1,322 @@
+// lloyd.cu -- Weighted Sort-Means (Algorithm 2) as one persistent cooperative kernel.
+//
+// Every pass runs on the device with no host round trip:
+//   A. assignment: each block owns a contiguous slice of the unique colours (in key
+//      order, so neighbouring threads hold similar colours).  A point starts at its
+//      previous centre p and scans row p of the sorted centre-distance table; the
+//      scan stops at the first centre t with d(c_p, c_t) > 4 d(x, c_p) (1 + 2^-17)
+//      (Section 2.2, item 3: if 2 d(x, c_p) <= d(c_p, c_t) then c_t is no nearer).
+//      The widened bound and a row table rounded down make the stop conservative
+//      under FP32 rounding, so the labels equal a full FP32 search with the lowest
+//      index winning ties.  Each block accumulates exact int64 sums
+//      (w R, w G, w B, w) per cluster in shared memory, its FP64 SSE partial and
+//      its distance count.
+//   -- grid barrier --
+//   B. update (every block, redundantly and identically): centres = S / W in FP64
+//      (an empty cluster keeps its centre), SSE_i = fixed-order sum of the block
+//      partials, the stopping test of Section 3.3.  Block 0 writes the outputs.
+//   C. table: rows of squared centre-to-centre distances, each sorted ascending
+//      and packed as (distance bits with the low 8 cleared) | index, built one row
+//      per block.
+//   -- grid barrier --
+#include "kq_dev.cuh"
+
+namespace kq {
+namespace {
+
+constexpr int kLloydBlock = 512;
+constexpr int kPtsPerThread = 4;  // blocks used = ceil(N' / (block * this)), capped by the launch
+constexpr float kPruneSlack = 1.0f + 0x1p-17f;
+constexpr unsigned kFull = 0xffffffffu;
+
+struct LloydArgs {
+    const uint32_t *keys;
+    const uint32_t *w;
+    const int32_t *n_unique;
+    int K;
+    double eps;
+    int max_iter;
+    uint32_t flags;
+    int skip_if_n_le;
+    double *centers;
+    uint8_t *labels;
+    uint8_t *palette;
+    kq_lloyd_stats *stats;
+    double *sse_hist;
+    Ctl *ctl;
+    unsigned long long *sums;  // [3][kMaxK][4]: pass i adds into buffer i % 3
+    double *sse_part;          // [2][kMaxGrid]
+    uint32_t *rows;            // [K][K]
+};
+
+struct LloydShared {
+    float4 c[kMaxK];
+    double c64[kMaxK * 3];
+    unsigned long long sum[kMaxK * 4];
+    uint32_t row[kMaxK];
+    double red_d[kLloydBlock / 32];
+    unsigned long long red_u[kLloydBlock / 32];
+    double sse_i;
+};
+
+__device__ __forceinline__ void build_rows(LloydShared &sh, int K, int b, int G, uint32_t *rows)
+{
+    for (int p = b; p < K; p += G) {
+        const float4 cp = sh.c[p];
+        for (int t = threadIdx.x; t < K; t += kLloydBlock) {
+            const float4 ct = sh.c[t];
+            const float d = dist3(cp.x, cp.y, cp.z, ct.x, ct.y, ct.z);
+            sh.row[t] = (__float_as_uint(d) & 0xFFFFFF00u) | (uint32_t)t;
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < K; t += kLloydBlock) {
+            const uint32_t v = sh.row[t];
+            int r = 0;
+            for (int u = 0; u < K; ++u) r += (sh.row[u] < v) ? 1 : 0;
+            rows[(size_t)p * K + r] = v;
+        }
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ void warp_accumulate(LloydShared &sh, bool active, int arg, uint32_t w, uint32_t key)
+{
+    const int a0 = __shfl_sync(kFull, arg, 0);
+    const bool same = __all_sync(kFull, !active || arg == a0);
+    unsigned long long W = active ? (unsigned long long)w : 0ull;
+    unsigned long long r = W * key_r(key), g = W * key_g(key), bb = W * key_b(key);
+    if (same) {
+        for (int o = 16; o; o >>= 1) {
+            r += __shfl_down_sync(kFull, r, o);
+            g += __shfl_down_sync(kFull, g, o);
+            bb += __shfl_down_sync(kFull, bb, o);
+            W += __shfl_down_sync(kFull, W, o);
+        }
+        if ((threadIdx.x & 31) == 0 && W) {
+            atomicAdd(&sh.sum[a0 * 4 + 0], r);
+            atomicAdd(&sh.sum[a0 * 4 + 1], g);
+            atomicAdd(&sh.sum[a0 * 4 + 2], bb);
+            atomicAdd(&sh.sum[a0 * 4 + 3], W);
+        }
+    } else if (active) {
+        atomicAdd(&sh.sum[arg * 4 + 0], r);
+        atomicAdd(&sh.sum[arg * 4 + 1], g);
+        atomicAdd(&sh.sum[arg * 4 + 2], bb);
+        atomicAdd(&sh.sum[arg * 4 + 3], W);
+    }
+}
+
+__global__ void __launch_bounds__(kLloydBlock) lloyd_kernel(LloydArgs a)
+{
+    __shared__ LloydShared sh;
+    const int K = a.K;
+    const int64_t n = *a.n_unique;
+    if (a.skip_if_n_le > 0 && n <= a.skip_if_n_le) return;
+    int64_t want = (n + (int64_t)kLloydBlock * kPtsPerThread - 1) / ((int64_t)kLloydBlock * kPtsPerThread);
+    const int G = (int)(want < 1 ? 1 : (want > gridDim.x ? gridDim.x : want));
+    const int b = blockIdx.x;
+    if (b >= G) return;
+    Ctl *ctl = a.ctl;
+    const int tid = threadIdx.x;
+    const bool prune = !(a.flags & KQ_LLOYD_DENSE);
+    const bool labels_in = (a.flags & KQ_LLOYD_LABELS_IN) != 0;
+
+    for (int k = tid; k < K; k += kLloydBlock) {
+        const double x = a.centers[3 * k], y = a.centers[3 * k + 1], z = a.centers[3 * k + 2];
+        sh.c64[3 * k] = x;
+        sh.c64[3 * k + 1] = y;
+        sh.c64[3 * k + 2] = z;
+        sh.c[k] = make_float4((float)x, (float)y, (float)z, 0.f);
+    }
+    __syncthreads();
+    if (prune) build_rows(sh, K, b, G, a.rows);
+    if (b == 0) {
+        for (int j = tid; j < 3 * kMaxK * 4; j += kLloydBlock) a.sums[j] = 0ull;
+        if (tid == 0) ctl->ndc = 0ull;
+    }
+    if (!grid_sync(ctl, G)) return;
+
+    int64_t lo, hi;
+    slice_of(n, b, G, &lo, &hi);
+    double prev_sse = 0.0;
+    int it = 0;
+    for (;;) {
+        const int buf = it & 1;
+        unsigned long long *gsum = a.sums + (size_t)(it % 3) * kMaxK * 4;
+        for (int j = tid; j < K * 4; j += kLloydBlock) sh.sum[j] = 0ull;
+        __syncthreads();
+        const bool use_prev = prune && (labels_in || it > 0);
+        double sse = 0.0;
+        unsigned long long ndc = 0ull;
+        for (int64_t base = lo; base < hi; base += kLloydBlock) {
+            const int64_t i = base + tid;
+            const bool active = i < hi;
+            uint32_t key = 0u, w = 0u;
+            int arg = 0;
+            float best = 0.f;
+            if (active) {
+                key = a.keys[i];
+                w = a.w[i];
+                const float x = (float)key_r(key), y = (float)key_g(key), z = (float)key_b(key);
+                if (use_prev) {
+                    int p = a.labels[i];
+                    if (p >= K) p = 0;
+                    const float4 cp = sh.c[p];
+                    const float prev = dist3(x, y, z, cp.x, cp.y, cp.z);
+                    best = prev;
+                    arg = p;
+                    ++ndc;
+                    const float thr = __fmul_rn(4.0f * prev, kPruneSlack);
+                    const uint32_t *row = a.rows + (size_t)p * K;
+                    for (int j = 0; j < K; ++j) {
+                        const uint32_t e = row[j];
+                        if (__uint_as_float(e & 0xFFFFFF00u) > thr) break;
+                        const int t = (int)(e & 0xFFu);
+                        if (t == p) continue;
+                        const float4 ct = sh.c[t];
+                        const float d = dist3(x, y, z, ct.x, ct.y, ct.z);
+                        ++ndc;
+                        if (d < best || (d == best && t < arg)) {
+                            best = d;
+                            arg = t;
+                        }
+                    }
+                } else {
+                    best = __int_as_float(0x7f800000);
+                    for (int k = 0; k < K; ++k) {
+                        const float4 ct = sh.c[k];
+                        const float d = dist3(x, y, z, ct.x, ct.y, ct.z);
+                        if (d < best) {
+                            best = d;
+                            arg = k;
+                        }
+                    }
+                    ndc += (unsigned long long)K;
+                }
+                a.labels[i] = (uint8_t)arg;
+                sse += (double)w * (double)best;
+            }
+            warp_accumulate(sh, active, arg, w, key);
+        }
+        const double bsse = block_sum_f64<kLloydBlock>(sse, sh.red_d);
+        const unsigned long long bndc = block_sum_u64<kLloydBlock>(ndc, sh.red_u);
+        __syncthreads();
+        for (int j = tid; j < K * 4; j += kLloydBlock)
+            if (sh.sum[j]) atomicAdd(gsum + j, sh.sum[j]);
+        if (tid == 0) {
+            a.sse_part[(size_t)buf * kMaxGrid + b] = bsse;
+            atomicAdd(&ctl->ndc, bndc);
+        }
+        if (!grid_sync(ctl, G)) return;
+
+        // ---- B: update and stopping test (identical in every block)
+        ++it;
+        if (tid < 32) {
+            double s = 0.0;
+            for (int g = tid; g < G; g += 32) s += __ldcg(a.sse_part + (size_t)buf * kMaxGrid + g);
+            for (int o = 16; o; o >>= 1) s += __shfl_down_sync(kFull, s, o);
+            if (tid == 0) sh.sse_i = s;
+        }
+        for (int k = tid; k < K; k += kLloydBlock) {
+            const unsigned long long W = __ldcg(gsum + 4 * k + 3);
+            if (W) {
+                const double dw = (double)W;
+                const double x = (double)__ldcg(gsum + 4 * k) / dw;
+                const double y = (double)__ldcg(gsum + 4 * k + 1) / dw;
+                const double z = (double)__ldcg(gsum + 4 * k + 2) / dw;
+                sh.c64[3 * k] = x;
+                sh.c64[3 * k + 1] = y;
+                sh.c64[3 * k + 2] = z;
+                sh.c[k] = make_float4((float)x, (float)y, (float)z, 0.f);
+            }
+        }
+        __syncthreads();
+        const double sse_i = sh.sse_i;
+        bool conv = false;
+        if (a.eps >= 0.0) {
+            if (sse_i == 0.0) conv = true;
+            else if (it > 1 && (prev_sse - sse_i) / sse_i <= a.eps) conv = true;
+        }
+        const bool stop = conv || it >= a.max_iter;
+        if (b == 0) {
+            // Buffer (pass + 1) % 3 was read by every block in the previous pass, which
+            // all blocks finished before the barrier above, and is next added into two
+            // passes from now, after a barrier this block must reach first.  (The next
+            // pass's buffer was cleared one pass ago: without pruning there is no
+            // barrier between this update and the next pass's additions.)
+            unsigned long long *ahead = a.sums + (size_t)((it + 1) % 3) * kMaxK * 4;
+            for (int j = tid; j < kMaxK * 4; j += kLloydBlock) ahead[j] = 0ull;
+            if (tid == 0 && a.sse_hist) a.sse_hist[it - 1] = sse_i;
+            if (stop) {
+                for (int j = tid; j < 3 * K; j += kLloydBlock) a.centers[j] = sh.c64[j];
+                for (int k = tid; k < K; k += kLloydBlock) {
+                    const unsigned long long W = __ldcg(gsum + 4 * k + 3);
+                    for (int ch = 0; ch < 3; ++ch) {
+                        int v;
+                        if (W) {
+                            const unsigned long long S = __ldcg(gsum + 4 * k + ch);
+                            v = (int)((2ull * S + W) / (2ull * W));
+                        } else {
+                            const double f = floor(sh.c64[3 * k + ch] + 0.5);
+                            v = f < 0.0 ? 0 : (f > 255.0 ? 255 : (int)f);
+                        }
+                        a.palette[3 * k + ch] = (uint8_t)v;
+                    }
+                }
+                if (tid == 0 && a.stats) {
+                    kq_lloyd_stats st;
+                    st.iters = it;
+                    st.converged = conv ? 1 : 0;
+                    st.k_eff = (int32_t)(n < K ? n : K);
+                    st.status = *(volatile int32_t *)&ctl->status;
+                    st.ndc = (int64_t)*(volatile unsigned long long *)&ctl->ndc;
+                    st.sse = sse_i;
+                    st.sse_prev = it > 1 ? prev_sse : 0.0;
+                    *a.stats = st;
+                }
+            }
+        }
+        if (stop) return;
+        prev_sse = sse_i;
+        if (prune) {
+            build_rows(sh, K, b, G, a.rows);
+            if (!grid_sync(ctl, G)) return;
+        }
+    }
+}
+
+}  // namespace
+
+int launch_lloyd(const uint32_t *keys, const uint32_t *w, const int32_t *n_unique, int K, double *centers, double eps,
+                 int max_iter, uint32_t flags, uint8_t *labels, uint8_t *palette, kq_lloyd_stats *stats,
+                 double *sse_hist, void *ws, const Layout &L, cudaStream_t s, int skip_if_n_le)
+{
+    const DeviceInfo di = device_info();
+    int per_sm = max_coresident((const void *)lloyd_kernel, kLloydBlock, 0);
+    if (per_sm < 1) return KQ_ECUDA;
+    int grid = di.sms * per_sm;
+    if (grid > kMaxGrid) grid = kMaxGrid;
+    LloydArgs a;
+    a.keys = keys;
+    a.w = w;
+    a.n_unique = n_unique;
+    a.K = K;
+    a.eps = eps;
+    a.max_iter = max_iter;
+    a.flags = flags;
+    a.skip_if_n_le = skip_if_n_le;
+    a.centers = centers;
+    a.labels = labels;
+    a.palette = palette;
+    a.stats = stats;
+    a.sse_hist = sse_hist;
+    a.ctl = at<Ctl>(ws, L.ctl);
+    a.sums = at<unsigned long long>(ws, L.l_sums);
+    a.sse_part = at<double>(ws, L.l_sse);
+    a.rows = at<uint32_t>(ws, L.l_rows);
+    void *args[] = {&a};
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)lloyd_kernel, dim3(grid), dim3(kLloydBlock), args, 0, s);
+    return e == cudaSuccess ? KQ_OK : KQ_ECUDA;
+}
+
+}  // namespace kq

@@ -1,0 +1,779 @@
+// seed.cu -- the generic initialization schemes of Section 2.3 on the GPU.
+//
+// Every scheme except LBG picks unique colours, so its arithmetic is integer and
+// its result is exact.  Random draws follow the counter-based SplitMix64 streams
+// documented in kq.h: stream 1 Forgy, 2 k-means++, 3 minmax, 4/5 subset farthest
+// first, 16 + cell for the density scheme.
+//
+//   FGY  partial Fisher-Yates on one thread, the displaced entries in a shared
+//        memory hash map.
+//   KPP, MMX  one persistent cooperative kernel: per round every block refreshes
+//        its slice's nearest-centre distances (exact integers); KPP sums w D^2 per
+//        block and every block then finds the sampled colour from the block sums
+//        and the chosen block's slice; MMX takes a packed (D^2, lowest index)
+//        maximum with one atomic per block.  One grid barrier per round.
+//   SFF  one block: subset draw, sort, then minmax over the subset.
+//   VAR  per-chunk value counts and exact weighted moments, then one warp per
+//        group median locates the element of the requested rank.
+//   DEN  per-chunk cell counts, the seat apportionment on one thread, then one
+//        block per cell draws and locates its members.
+//   LBG  centroid, then split rounds that call the Lloyd kernel.
+#include <math.h>
+
+#include "kq_dev.cuh"
+
+namespace kq {
+namespace {
+
+constexpr int kFarBlock = 512;
+constexpr int kChunkBlock = 256;
+constexpr int kMapSlots = 8192;   // Fisher-Yates displacement map (positions + values)
+constexpr int kSffMax = 4096;     // ceil(2 * 256 * ln 256) = 2840 fits
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ void key_to_centre(double *c, uint32_t key)
+{
+    c[0] = (double)key_r(key);
+    c[1] = (double)key_g(key);
+    c[2] = (double)key_b(key);
+}
+
+// ---------------------------------------------------------------- K >= N'
+// The centres are the N' unique colours in key order, padded with the last.
+__global__ void seed_all_unique(const uint32_t *keys, const int32_t *n_unique, int K, double *centers)
+{
+    const int64_t n = *n_unique;
+    if (n > K) return;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        if (n == 0) {
+            centers[3 * k] = centers[3 * k + 1] = centers[3 * k + 2] = 0.0;
+        } else {
+            key_to_centre(centers + 3 * k, keys[k < n ? k : n - 1]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- Fisher-Yates
+struct FyMap {
+    uint32_t *pos1;  // position + 1, 0 = empty
+    uint32_t *val;
+    uint32_t mask;
+};
+
+__device__ __forceinline__ uint32_t fy_slot(uint32_t pos, uint32_t mask) { return (pos * 2654435761u) & mask; }
+
+__device__ uint32_t fy_get(const FyMap &m, uint32_t pos)
+{
+    for (uint32_t h = fy_slot(pos, m.mask);; h = (h + 1) & m.mask) {
+        if (m.pos1[h] == 0u) return pos;
+        if (m.pos1[h] == pos + 1u) return m.val[h];
+    }
+}
+
+__device__ void fy_set(const FyMap &m, uint32_t pos, uint32_t v)
+{
+    uint32_t h = fy_slot(pos, m.mask);
+    while (m.pos1[h] != 0u && m.pos1[h] != pos + 1u) h = (h + 1) & m.mask;
+    m.pos1[h] = pos + 1u;
+    m.val[h] = v;
+}
+
+// The first `count` entries of a uniformly random permutation of 0..n-1
+// (single thread; the map must hold 2 * count entries).
+__device__ void fisher_yates(uint32_t n, uint32_t count, uint64_t seed, uint32_t stream, const FyMap &m, uint32_t *out)
+{
+    for (uint32_t j = 0; j < count; ++j) {
+        const uint32_t r = j + (uint32_t)below(rand64(seed, stream, j), (uint64_t)(n - j));
+        const uint32_t vj = fy_get(m, j), vr = fy_get(m, r);
+        fy_set(m, j, vr);
+        fy_set(m, r, vj);
+        out[j] = vr;
+    }
+}
+
+__device__ void clear_map(uint32_t *pos1, int slots)
+{
+    for (int i = threadIdx.x; i < slots; i += blockDim.x) pos1[i] = 0u;
+}
+
+// Forgy: K distinct unique colours drawn uniformly (Algorithm 2, first line).
+__global__ void seed_fgy(const uint32_t *keys, const int32_t *n_unique, int K, uint64_t seed, double *centers)
+{
+    extern __shared__ uint32_t smem[];
+    const int64_t n = *n_unique;
+    if (n <= K) return;
+    FyMap m{smem, smem + kMapSlots, kMapSlots - 1};
+    uint32_t *pick = smem + 2 * kMapSlots;
+    clear_map(m.pos1, kMapSlots);
+    __syncthreads();
+    if (threadIdx.x == 0) fisher_yates((uint32_t)n, (uint32_t)K, seed, 1, m, pick);
+    __syncthreads();
+    for (int k = threadIdx.x; k < K; k += blockDim.x) key_to_centre(centers + 3 * k, keys[pick[k]]);
+}
+
+// ---------------------------------------------------------------- SFF
+// Minmax on a uniform random subset of size min(N', s0), s0 = max(K, ceil(2 K ln K)).
+// The subset is taken in ascending index order; ties go to the lowest index.
+constexpr int kSffBlock = 256;
+
+__global__ void __launch_bounds__(kSffBlock) seed_sff(const uint32_t *keys, const int32_t *n_unique, int K,
+                                                      uint64_t seed, int s0, double *centers)
+{
+    extern __shared__ uint32_t smem[];
+    __shared__ unsigned long long s_red[kSffBlock / 32];
+    __shared__ uint32_t s_cur;
+    const int64_t n = *n_unique;
+    if (n <= K) return;
+    const uint32_t s = (uint32_t)(s0 < n ? s0 : n);
+    FyMap m{smem, smem + kMapSlots, kMapSlots - 1};
+    uint32_t *sub = smem + 2 * kMapSlots;   // kSffMax entries
+    uint32_t *mind = sub + kSffMax;         // kSffMax entries
+    clear_map(m.pos1, kMapSlots);
+    __syncthreads();
+    if (threadIdx.x == 0) fisher_yates((uint32_t)n, s, seed, 4, m, sub);
+    __syncthreads();
+    for (uint32_t i = s + threadIdx.x; i < kSffMax; i += kSffBlock) sub[i] = 0xFFFFFFFFu;
+    __syncthreads();
+    // bitonic sort of kSffMax entries, ascending
+    for (int size = 2; size <= kSffMax; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < kSffMax; i += kSffBlock) {
+                const int j = i ^ stride;
+                if (j > i) {
+                    const bool up = (i & size) == 0;
+                    const uint32_t a = sub[i], b = sub[j];
+                    if ((a > b) == up) {
+                        sub[i] = b;
+                        sub[j] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (threadIdx.x == 0) s_cur = (uint32_t)below(rand64(seed, 5, 0), (uint64_t)s);
+    __syncthreads();
+    uint32_t cur = s_cur;
+    if (threadIdx.x == 0) key_to_centre(centers, keys[sub[cur]]);
+    for (int k = 1; k < K; ++k) {
+        const uint32_t ck = keys[sub[cur]];
+        unsigned long long best = 0ull;
+        for (uint32_t i = threadIdx.x; i < s; i += kSffBlock) {
+            const uint32_t d = key_dist2(keys[sub[i]], ck);
+            const uint32_t md = (k == 1) ? d : min(mind[i], d);
+            mind[i] = md;
+            const unsigned long long packed = ((unsigned long long)md << 32) | (0xFFFFFFFFu - i);
+            best = packed > best ? packed : best;
+        }
+        for (int o = 16; o; o >>= 1) {
+            const unsigned long long other = __shfl_down_sync(kFull, best, o);
+            best = other > best ? other : best;
+        }
+        if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = best;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long b = 0ull;
+            for (int wv = 0; wv < kSffBlock / 32; ++wv) b = s_red[wv] > b ? s_red[wv] : b;
+            s_cur = 0xFFFFFFFFu - (uint32_t)(b & 0xFFFFFFFFull);
+            key_to_centre(centers + 3 * k, keys[sub[s_cur]]);
+        }
+        __syncthreads();
+        cur = s_cur;
+    }
+}
+
+// ---------------------------------------------------------------- KPP / MMX
+struct FarArgs {
+    const uint32_t *keys;
+    const uint32_t *w;
+    const int32_t *n_unique;
+    int K;
+    int mode;  // 0 = k-means++, 1 = minmax
+    uint64_t seed;
+    int64_t max_unique;
+    double *centers;
+    Ctl *ctl;
+    uint32_t *d2;              // [2][max_unique]
+    unsigned long long *part;  // [2][kMaxGrid]
+    unsigned long long *slot;  // [kMaxK]
+};
+
+struct FarShared {
+    unsigned long long red[kFarBlock / 32];
+    unsigned long long scan[kFarBlock / 32];
+    unsigned long long found;
+    uint32_t cur;
+    int gstar;
+    unsigned long long resid;
+};
+
+// Sampling by inverse CDF: with total = sum of the G block partials part[] and
+// t = below(u, total), the index of the first item whose running sum of
+// `value` exceeds t.  The block is found from the partials, the item inside that
+// block's slice.  Every block computes the same answer.
+template <typename V>
+__device__ uint32_t locate(FarShared &sh, const unsigned long long *part, int G, int64_t n, uint64_t u, V value)
+{
+    const int tid = threadIdx.x;
+    if (tid < 32) {
+        unsigned long long total = 0ull;
+        for (int g = tid; g < G; g += 32) total += __ldcg(part + g);
+        for (int o = 16; o; o >>= 1) total += __shfl_xor_sync(kFull, total, o);
+        const unsigned long long t = below(u, total);
+        // first g with prefix(part[0..g]) > t, 32 partials at a time
+        unsigned long long run = 0ull;
+        int gstar = G - 1;
+        unsigned long long resid = 0ull;
+        bool done = false;
+        for (int base = 0; base < G && !done; base += 32) {
+            const int g = base + tid;
+            const unsigned long long v = g < G ? __ldcg(part + g) : 0ull;
+            unsigned long long x = v;
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(kFull, x, o);
+                if (tid >= o) x += y;
+            }
+            const bool hit = g < G && run + x > t;
+            const unsigned bal = __ballot_sync(kFull, hit);
+            if (bal) {
+                const int l = __ffs(bal) - 1;
+                const unsigned long long xl = __shfl_sync(kFull, x, l);
+                const unsigned long long vl = __shfl_sync(kFull, v, l);
+                gstar = base + l;
+                resid = t - (run + xl - vl);
+                done = true;
+            } else {
+                run += __shfl_sync(kFull, x, 31);
+            }
+        }
+        if (tid == 0) {
+            sh.gstar = gstar;
+            sh.resid = resid;
+            sh.found = ~0ull;
+        }
+    }
+    __syncthreads();
+    const int gstar = sh.gstar;
+    const unsigned long long resid = sh.resid;
+    int64_t lo, hi;
+    slice_of(n, gstar, G, &lo, &hi);
+    unsigned long long run = 0ull;
+    for (int64_t base = lo; base < hi; base += kFarBlock) {
+        const int64_t i = base + tid;
+        const unsigned long long v = i < hi ? value(i) : 0ull;
+        unsigned long long tot;
+        const unsigned long long ex = block_excl_scan_u64<kFarBlock>(v, sh.scan, &tot);
+        if (i < hi && run + ex <= resid && run + ex + v > resid) sh.found = (unsigned long long)i;
+        __syncthreads();
+        if (sh.found != ~0ull) break;
+        run += tot;
+    }
+    __syncthreads();
+    unsigned long long f = sh.found;
+    if (f == ~0ull) f = (unsigned long long)(hi > lo ? hi - 1 : 0);  // unreachable with exact sums
+    return (uint32_t)f;
+}
+
+__global__ void __launch_bounds__(kFarBlock) seed_far(FarArgs a)
+{
+    __shared__ FarShared sh;
+    const int64_t n = *a.n_unique;
+    if (n <= a.K) return;
+    const int K = a.K;
+    int64_t want = (n + (int64_t)kFarBlock * 4 - 1) / ((int64_t)kFarBlock * 4);
+    const int G = (int)(want < 1 ? 1 : (want > gridDim.x ? gridDim.x : want));
+    const int b = blockIdx.x;
+    if (b >= G) return;
+    Ctl *ctl = a.ctl;
+    if (n > a.max_unique) {
+        if (b == 0 && threadIdx.x == 0) fail(ctl, KQ_ENOMEM);
+        return;
+    }
+    const int tid = threadIdx.x;
+    int64_t lo, hi;
+    slice_of(n, b, G, &lo, &hi);
+    if (b == 0)
+        for (int k = tid; k < kMaxK; k += kFarBlock) a.slot[k] = 0ull;
+    uint32_t cur;
+    if (a.mode == 0) {
+        unsigned long long s = 0ull;
+        for (int64_t i = lo + tid; i < hi; i += kFarBlock) s += a.w[i];
+        s = block_sum_u64<kFarBlock>(s, sh.red);
+        if (tid == 0) a.part[b] = s;
+        if (!grid_sync(ctl, G)) return;
+        cur = locate(sh, a.part, G, n, rand64(a.seed, 2, 0),
+                     [&](int64_t i) { return (unsigned long long)__ldcg(a.w + i); });
+    } else {
+        if (!grid_sync(ctl, G)) return;
+        cur = (uint32_t)below(rand64(a.seed, 3, 0), (uint64_t)n);
+    }
+    if (b == 0 && tid == 0) key_to_centre(a.centers, a.keys[cur]);
+    for (int r = 1; r < K; ++r) {
+        const uint32_t ck = __ldcg(a.keys + cur);
+        // D^2 alternates between two buffers: other blocks may still be reading this
+        // round's buffer (to locate the sample) while this block starts the next round.
+        uint32_t *d2 = a.d2 + (size_t)(r & 1) * (size_t)a.max_unique;
+        const uint32_t *d2_prev = a.d2 + (size_t)((r - 1) & 1) * (size_t)a.max_unique;
+        unsigned long long acc = 0ull;
+        for (int64_t i = lo + tid; i < hi; i += kFarBlock) {
+            const uint32_t d = key_dist2(a.keys[i], ck);
+            const uint32_t md = (r == 1) ? d : min(d2_prev[i], d);
+            d2[i] = md;
+            if (a.mode == 0) {
+                acc += (unsigned long long)a.w[i] * md;
+            } else {
+                const unsigned long long packed = ((unsigned long long)md << 32) | (0xFFFFFFFFu - (uint32_t)i);
+                acc = packed > acc ? packed : acc;
+            }
+        }
+        unsigned long long *part = a.part + (size_t)(r & 1) * kMaxGrid;
+        if (a.mode == 0) {
+            const unsigned long long s = block_sum_u64<kFarBlock>(acc, sh.red);
+            if (tid == 0) part[b] = s;
+        } else {
+            for (int o = 16; o; o >>= 1) {
+                const unsigned long long other = __shfl_down_sync(kFull, acc, o);
+                acc = other > acc ? other : acc;
+            }
+            if ((tid & 31) == 0 && acc) atomicMax(a.slot + r, acc);
+        }
+        if (!grid_sync(ctl, G)) return;
+        if (a.mode == 0) {
+            cur = locate(sh, part, G, n, rand64(a.seed, 2, (uint32_t)r), [&](int64_t i) {
+                return (unsigned long long)__ldcg(a.w + i) * (unsigned long long)__ldcg(d2 + i);
+            });
+        } else {
+            cur = 0xFFFFFFFFu - (uint32_t)(__ldcg(a.slot + r) & 0xFFFFFFFFull);
+        }
+        if (b == 0 && tid == 0) key_to_centre(a.centers + 3 * r, __ldcg(a.keys + cur));
+    }
+}
+
+// ---------------------------------------------------------------- chunked counts (VAR, DEN)
+__device__ __forceinline__ int den_cell(uint32_t key)
+{
+    return (int)(((key >> 22) & 3u) * 16u + ((key >> 14) & 3u) * 4u + ((key >> 6) & 3u));
+}
+
+__device__ __forceinline__ int64_t chunk_len(int64_t n) { return (n + kSeedChunks - 1) / kSeedChunks; }
+
+// mode 0 (VAR): per chunk, counts of each value of each channel; exact moments.
+// mode 1 (DEN): per chunk, counts per cell; pixel weight and colour count per cell.
+__global__ void __launch_bounds__(kChunkBlock) seed_chunk_counts(const uint32_t *keys, const uint32_t *w,
+                                                                 const int32_t *n_unique, int K, int mode,
+                                                                 uint32_t *chunk_cnt, uint32_t *gcnt,
+                                                                 unsigned long long *cell_w, Ctl *ctl)
+{
+    __shared__ uint32_t s_cnt[3 * 256];
+    __shared__ unsigned long long s_w[kDenCells];
+    __shared__ unsigned long long s_red[kChunkBlock / 32];
+    const int64_t n = *n_unique;
+    if (n <= K) return;
+    const int c = blockIdx.x;
+    const int64_t len = chunk_len(n);
+    const int64_t lo = (int64_t)c * len < n ? (int64_t)c * len : n;
+    const int64_t hi = lo + len < n ? lo + len : n;
+    for (int i = threadIdx.x; i < 3 * 256; i += kChunkBlock) s_cnt[i] = 0u;
+    for (int i = threadIdx.x; i < kDenCells; i += kChunkBlock) s_w[i] = 0ull;
+    __syncthreads();
+    unsigned long long mw = 0, m1[3] = {0, 0, 0}, m2[3] = {0, 0, 0};
+    for (int64_t i = lo + threadIdx.x; i < hi; i += kChunkBlock) {
+        const uint32_t key = keys[i];
+        const unsigned long long wi = w[i];
+        if (mode == 0) {
+            const uint32_t x[3] = {key_r(key), key_g(key), key_b(key)};
+            mw += wi;
+            for (int ch = 0; ch < 3; ++ch) {
+                atomicAdd(&s_cnt[ch * 256 + x[ch]], 1u);
+                m1[ch] += wi * x[ch];
+                m2[ch] += wi * x[ch] * x[ch];
+            }
+        } else {
+            const int cell = den_cell(key);
+            atomicAdd(&s_cnt[cell], 1u);
+            atomicAdd(&s_w[cell], wi);
+        }
+    }
+    __syncthreads();
+    const int width = mode == 0 ? 3 * 256 : kDenCells;
+    for (int i = threadIdx.x; i < width; i += kChunkBlock) {
+        chunk_cnt[(size_t)c * width + i] = s_cnt[i];
+        if (s_cnt[i]) atomicAdd(&gcnt[i], s_cnt[i]);
+        if (mode == 1 && s_w[i]) atomicAdd(&cell_w[i], s_w[i]);
+    }
+    if (mode == 0) {
+        unsigned long long t = block_sum_u64<kChunkBlock>(mw, s_red);
+        if (threadIdx.x == 0 && t) atomicAdd(&ctl->var_w, t);
+        for (int ch = 0; ch < 3; ++ch) {
+            t = block_sum_u64<kChunkBlock>(m1[ch], s_red);
+            if (threadIdx.x == 0 && t) atomicAdd(&ctl->var_s1[ch], t);
+            t = block_sum_u64<kChunkBlock>(m2[ch], s_red);
+            if (threadIdx.x == 0 && t) atomicAdd(&ctl->var_s2[ch], t);
+        }
+    }
+}
+
+// Warp-level: index of the element of rank `j` (0-based, in key order) among the
+// unique colours whose class (channel value or cell) equals `cls`.
+__device__ int64_t warp_locate(const uint32_t *keys, int64_t n, const uint32_t *chunk_cnt, int width, int col,
+                               uint32_t j, int mode, int ch)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t len = chunk_len(n);
+    // chunk holding the element
+    uint32_t run = 0;
+    int cstar = kSeedChunks - 1;
+    for (int base = 0; base < kSeedChunks; base += 32) {
+        const uint32_t v = chunk_cnt[(size_t)(base + lane) * width + col];
+        uint32_t x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x += y;
+        }
+        const unsigned bal = __ballot_sync(kFull, run + x > j);
+        if (bal) {
+            const int l = __ffs(bal) - 1;
+            cstar = base + l;
+            run += __shfl_sync(kFull, x, l) - __shfl_sync(kFull, v, l);
+            break;
+        }
+        run += __shfl_sync(kFull, x, 31);
+    }
+    uint32_t r = j - run;
+    const int64_t lo = (int64_t)cstar * len, hi = lo + len < n ? lo + len : n;
+    for (int64_t base = lo; base < hi; base += 32) {
+        const int64_t i = base + lane;
+        bool match = false;
+        if (i < hi) {
+            const uint32_t key = keys[i];
+            match = mode == 0 ? (int)((key >> (16 - 8 * ch)) & 255u) == col - ch * 256 : den_cell(key) == col;
+        }
+        const unsigned bal = __ballot_sync(kFull, match);
+        const uint32_t c = __popc(bal);
+        if (r < c) {
+            unsigned m = bal;
+            for (uint32_t q = 0; q < r; ++q) m &= m - 1;
+            return base + (__ffs(m) - 1);
+        }
+        r -= c;
+    }
+    return hi > 0 ? hi - 1 : 0;  // unreachable with consistent counts
+}
+
+// ---------------------------------------------------------------- VAR
+__global__ void seed_var_pick(const uint32_t *keys, const int32_t *n_unique, int K, const uint32_t *chunk_cnt,
+                              const uint32_t *gcnt, const Ctl *ctl, double *centers)
+{
+    const int64_t n = *n_unique;
+    if (n <= K) return;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= K) return;
+    // channel of largest weighted variance, compared as W * S2 - S1^2 (exact)
+    const unsigned __int128 W = ctl->var_w;
+    int ch = 0;
+    unsigned __int128 best = 0;
+    for (int c = 0; c < 3; ++c) {
+        const unsigned __int128 s1 = ctl->var_s1[c], s2 = ctl->var_s2[c];
+        const unsigned __int128 v = W * s2 - s1 * s1;
+        if (c == 0 || v > best) {
+            best = v;
+            ch = c;
+        }
+    }
+    const int g = warp;
+    const int64_t glo = (int64_t)g * n / K, ghi = (int64_t)(g + 1) * n / K;
+    const uint32_t m = (uint32_t)((glo + ghi - 1) / 2);
+    // value v holding rank m
+    uint32_t run = 0;
+    int v = 255;
+    for (int base = 0; base < 256; base += 32) {
+        const uint32_t cv = gcnt[ch * 256 + base + lane];
+        uint32_t x = cv;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x += y;
+        }
+        const unsigned bal = __ballot_sync(kFull, run + x > m);
+        if (bal) {
+            const int l = __ffs(bal) - 1;
+            v = base + l;
+            run += __shfl_sync(kFull, x, l) - __shfl_sync(kFull, cv, l);
+            break;
+        }
+        run += __shfl_sync(kFull, x, 31);
+    }
+    const int64_t idx = warp_locate(keys, n, chunk_cnt, 3 * 256, ch * 256 + v, m - run, 0, ch);
+    if (lane == 0) key_to_centre(centers + 3 * g, keys[idx]);
+}
+
+// ---------------------------------------------------------------- DEN
+// Seats in proportion to each cell's pixel count by largest remainder (ties to
+// the lower cell); a cell whose share exceeds its colour count is fixed at that
+// count and the remaining seats are shared again among the other cells.
+__global__ void seed_den_quota(const int32_t *n_unique, int K, const uint32_t *celln_in,
+                               const unsigned long long *cellw, int *quota_out)
+{
+    const int64_t n = *n_unique;
+    if (n <= K || threadIdx.x != 0) return;
+    int64_t celln[kDenCells], q[kDenCells], rem[kDenCells];
+    int fixed[kDenCells];
+    for (int c = 0; c < kDenCells; ++c) {
+        celln[c] = celln_in[c];
+        fixed[c] = 0;
+    }
+    for (;;) {
+        int64_t seats = K;
+        unsigned long long wa = 0;
+        for (int c = 0; c < kDenCells; ++c) {
+            if (fixed[c]) seats -= celln[c];
+            else if (celln[c] > 0) wa += cellw[c];
+        }
+        int64_t given = 0;
+        for (int c = 0; c < kDenCells; ++c) {
+            q[c] = 0;
+            rem[c] = -1;
+            if (fixed[c]) {
+                q[c] = celln[c];
+            } else if (celln[c] > 0 && wa > 0) {
+                const unsigned long long num = (unsigned long long)seats * cellw[c];
+                q[c] = (int64_t)(num / wa);
+                rem[c] = (int64_t)(num % wa);
+                given += q[c];
+            }
+        }
+        for (int64_t left = seats - given; left > 0; --left) {
+            int arg = -1;
+            for (int c = 0; c < kDenCells; ++c)
+                if (rem[c] >= 0 && (arg < 0 || rem[c] > rem[arg])) arg = c;
+            q[arg] += 1;
+            rem[arg] = -1;
+        }
+        int grew = 0;
+        for (int c = 0; c < kDenCells; ++c) {
+            if (!fixed[c] && q[c] > celln[c]) {
+                fixed[c] = 1;
+                grew = 1;
+            }
+        }
+        if (!grew) break;
+    }
+    int off = 0;
+    for (int c = 0; c < kDenCells; ++c) {
+        quota_out[c] = (int)q[c];
+        quota_out[kDenCells + c] = off;
+        off += (int)q[c];
+    }
+}
+
+// One block per cell: a uniform draw without replacement among the cell's
+// colours (stream 16 + cell), then one warp per pick locates the colour.
+__global__ void seed_den_pick(const uint32_t *keys, const int32_t *n_unique, int K, uint64_t seed,
+                              const uint32_t *chunk_cnt, const uint32_t *celln, const int *quota, double *centers)
+{
+    __shared__ uint32_t s_pos1[1024], s_val[1024], s_pick[kMaxK];
+    const int64_t n = *n_unique;
+    if (n <= K) return;
+    const int cell = blockIdx.x;
+    const int q = quota[cell];
+    if (q == 0) return;
+    const int off = quota[kDenCells + cell];
+    FyMap m{s_pos1, s_val, 1023u};
+    clear_map(s_pos1, 1024);
+    __syncthreads();
+    if (threadIdx.x == 0) fisher_yates(celln[cell], (uint32_t)q, seed, 16u + (uint32_t)cell, m, s_pick);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int j = warp; j < q; j += nw) {
+        const int64_t idx = warp_locate(keys, n, chunk_cnt, kDenCells, cell, s_pick[j], 1, 0);
+        if ((threadIdx.x & 31) == 0) key_to_centre(centers + 3 * (off + j), keys[idx]);
+    }
+}
+
+// ---------------------------------------------------------------- LBG
+__global__ void seed_lbg_start(const int32_t *n_unique, int K, const Ctl *ctl, double *centers)
+{
+    const int64_t n = *n_unique;
+    if (n <= K || threadIdx.x != 0) return;
+    const double W = (double)ctl->var_w;
+    for (int ch = 0; ch < 3; ++ch) centers[ch] = (double)ctl->var_s1[ch] / W;
+}
+
+// Per-cluster S (3), W and Q = sum w |x|^2 of the current labels.
+__global__ void seed_lbg_cluster_sums(const uint32_t *keys, const uint32_t *w, const int32_t *n_unique, int K,
+                                      const uint8_t *labels, unsigned long long *cs)
+{
+    const int64_t n = *n_unique;
+    if (n <= K) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t key = keys[i];
+        const unsigned long long wi = w[i];
+        const unsigned long long r = key_r(key), g = key_g(key), bb = key_b(key);
+        unsigned long long *c = cs + 5 * labels[i];
+        atomicAdd(c + 0, wi * r);
+        atomicAdd(c + 1, wi * g);
+        atomicAdd(c + 2, wi * bb);
+        atomicAdd(c + 3, wi);
+        atomicAdd(c + 4, wi * (r * r + g * g + bb * bb));
+    }
+}
+
+// Exact per-cluster SSE about the mean is num / W with num = W Q - |S|^2.
+__device__ __forceinline__ bool sse_greater(unsigned __int128 na, unsigned long long wa, unsigned __int128 nb,
+                                            unsigned long long wb)
+{
+    if (wa == 0) return false;
+    if (wb == 0) return true;
+    return na * (unsigned __int128)wb > nb * (unsigned __int128)wa;
+}
+
+// Split round: c_j - eps stays at j, c_j + eps goes to m + q (q-th chosen, in
+// ascending j).  All clusters split when 2m <= K; otherwise the K - m clusters
+// of largest SSE (ties to the lower index).
+__global__ void seed_lbg_split(const int32_t *n_unique, int K, int m, double eps,
+                               const unsigned long long *cs, double *centers)
+{
+    const int64_t n = *n_unique;
+    if (n <= K || threadIdx.x != 0) return;
+    const int split = (2 * m <= K) ? m : K - m;
+    bool chosen[kMaxK];
+    for (int j = 0; j < m; ++j) chosen[j] = split == m;
+    if (split < m) {
+        for (int t = 0; t < split; ++t) {
+            int arg = -1;
+            unsigned __int128 na = 0;
+            unsigned long long wa = 0;
+            for (int k = 0; k < m; ++k) {
+                if (chosen[k]) continue;
+                const unsigned long long W = cs[5 * k + 3];
+                unsigned __int128 s2 = 0;
+                for (int ch = 0; ch < 3; ++ch) s2 += (unsigned __int128)cs[5 * k + ch] * cs[5 * k + ch];
+                const unsigned __int128 num = (unsigned __int128)W * cs[5 * k + 4] - s2;
+                if (arg < 0 || sse_greater(num, W, na, wa)) {
+                    arg = k;
+                    na = num;
+                    wa = W;
+                }
+            }
+            chosen[arg] = true;
+        }
+    }
+    int q = 0;
+    for (int j = 0; j < m; ++j) {
+        if (!chosen[j]) continue;
+        for (int ch = 0; ch < 3; ++ch) {
+            const double base = centers[3 * j + ch];
+            centers[3 * (m + q) + ch] = base + eps;
+            centers[3 * j + ch] = base - eps;
+        }
+        ++q;
+    }
+}
+
+template <typename KFn>
+int set_smem(KFn kernel, size_t bytes)
+{
+    return cudaFuncSetAttribute((const void *)kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) ==
+                   cudaSuccess
+               ? 0
+               : -1;
+}
+
+}  // namespace
+
+int launch_seed(const uint32_t *keys, const uint32_t *w, const int32_t *n_unique, int K, int scheme, uint64_t seed,
+                const kq_seed_params &p, double *centers, void *ws, const Layout &L, cudaStream_t s)
+{
+    Ctl *ctl = at<Ctl>(ws, L.ctl);
+    seed_all_unique<<<1, 256, 0, s>>>(keys, n_unique, K, centers);
+    uint32_t *chunk_cnt = at<uint32_t>(ws, L.s_chunk);
+    uint32_t *gcnt = at<uint32_t>(ws, L.s_gcnt);
+    unsigned long long *cellw = reinterpret_cast<unsigned long long *>(gcnt + 3 * 256);
+    switch (scheme) {
+    case KQ_INIT_FGY: {
+        const size_t smem = sizeof(uint32_t) * (2 * kMapSlots + kMaxK);
+        if (set_smem(seed_fgy, smem)) return KQ_ECUDA;
+        seed_fgy<<<1, 32, smem, s>>>(keys, n_unique, K, seed, centers);
+        break;
+    }
+    case KQ_INIT_SFF: {
+        const size_t smem = sizeof(uint32_t) * (2 * kMapSlots + 2 * kSffMax);
+        if (set_smem(seed_sff, smem)) return KQ_ECUDA;
+        int s0 = (int)ceil(2.0 * K * log((double)K));
+        if (s0 < K) s0 = K;
+        seed_sff<<<1, kSffBlock, smem, s>>>(keys, n_unique, K, seed, s0, centers);
+        break;
+    }
+    case KQ_INIT_KPP:
+    case KQ_INIT_MMX: {
+        const DeviceInfo di = device_info();
+        const int per_sm = max_coresident((const void *)seed_far, kFarBlock, 0);
+        if (per_sm < 1) return KQ_ECUDA;
+        int grid = di.sms * per_sm;
+        if (grid > kMaxGrid) grid = kMaxGrid;
+        FarArgs a;
+        a.keys = keys;
+        a.w = w;
+        a.n_unique = n_unique;
+        a.K = K;
+        a.mode = scheme == KQ_INIT_KPP ? 0 : 1;
+        a.seed = seed;
+        a.max_unique = L.max_unique;
+        a.centers = centers;
+        a.ctl = ctl;
+        a.d2 = at<uint32_t>(ws, L.s_d2);
+        a.part = at<unsigned long long>(ws, L.s_part);
+        a.slot = at<unsigned long long>(ws, L.s_slot);
+        void *args[] = {&a};
+        if (cudaLaunchCooperativeKernel((const void *)seed_far, dim3(grid), dim3(kFarBlock), args, 0, s) != cudaSuccess)
+            return KQ_ECUDA;
+        break;
+    }
+    case KQ_INIT_VAR: {
+        if (cudaMemsetAsync(gcnt, 0, sizeof(uint32_t) * 3 * 256, s) != cudaSuccess) return KQ_ECUDA;
+        if (cudaMemsetAsync(&ctl->var_w, 0, sizeof(unsigned long long) * 7, s) != cudaSuccess) return KQ_ECUDA;
+        seed_chunk_counts<<<kSeedChunks, kChunkBlock, 0, s>>>(keys, w, n_unique, K, 0, chunk_cnt, gcnt, cellw, ctl);
+        seed_var_pick<<<(K * 32 + 255) / 256, 256, 0, s>>>(keys, n_unique, K, chunk_cnt, gcnt, ctl, centers);
+        break;
+    }
+    case KQ_INIT_DEN: {
+        int *quota = at<int>(ws, L.s_misc);
+        if (cudaMemsetAsync(gcnt, 0, sizeof(uint32_t) * 3 * 256 + sizeof(unsigned long long) * kDenCells, s) !=
+            cudaSuccess)
+            return KQ_ECUDA;
+        seed_chunk_counts<<<kSeedChunks, kChunkBlock, 0, s>>>(keys, w, n_unique, K, 1, chunk_cnt, gcnt, cellw, ctl);
+        seed_den_quota<<<1, 32, 0, s>>>(n_unique, K, gcnt, cellw, quota);
+        seed_den_pick<<<kDenCells, 256, 0, s>>>(keys, n_unique, K, seed, chunk_cnt, gcnt, quota, centers);
+        break;
+    }
+    case KQ_INIT_LBG: {
+        if (cudaMemsetAsync(gcnt, 0, sizeof(uint32_t) * 3 * 256, s) != cudaSuccess) return KQ_ECUDA;
+        if (cudaMemsetAsync(&ctl->var_w, 0, sizeof(unsigned long long) * 7, s) != cudaSuccess) return KQ_ECUDA;
+        seed_chunk_counts<<<kSeedChunks, kChunkBlock, 0, s>>>(keys, w, n_unique, K, 0, chunk_cnt, gcnt, cellw, ctl);
+        seed_lbg_start<<<1, 32, 0, s>>>(n_unique, K, ctl, centers);
+        unsigned long long *cs = at<unsigned long long>(ws, L.s_misc);
+        uint8_t *labels = at<uint8_t>(ws, L.s_labels);
+        uint8_t *pal = at<uint8_t>(ws, L.s_misc) + 32768;
+        const DeviceInfo di = device_info();
+        int m = 1;
+        while (m < K) {
+            const int split = (2 * m <= K) ? m : K - m;
+            if (split < m) {
+                if (cudaMemsetAsync(cs, 0, sizeof(unsigned long long) * 5 * kMaxK, s) != cudaSuccess) return KQ_ECUDA;
+                seed_lbg_cluster_sums<<<di.sms * 4, 256, 0, s>>>(keys, w, n_unique, K, labels, cs);
+            }
+            seed_lbg_split<<<1, 32, 0, s>>>(n_unique, K, m, p.lbg_eps, cs, centers);
+            m += split;
+            int st = launch_lloyd(keys, w, n_unique, m, centers, p.conv_eps, p.max_iter, 0u, labels, pal, nullptr,
+                                  nullptr, ws, L, s, K);
+            if (st != KQ_OK) return st;
+        }
+        break;
+    }
+    default:
+        return KQ_EINVAL;
+    }
+    return cudaGetLastError() == cudaSuccess ? KQ_OK : KQ_ECUDA;
+}
+
+}  // namespace kq

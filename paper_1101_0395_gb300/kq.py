@@ -1,0 +1,251 @@
+"""Python binding of libkq (include/kq.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and passes
+device pointers of torch CUDA tensors plus the current CUDA stream.  No step of
+the quantizer runs in Python or on the CPU: if libkq.so cannot be loaded, every
+call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+KQ_OK, KQ_EINVAL, KQ_ECAPACITY, KQ_ECUDA, KQ_ETIMEOUT, KQ_ENOMEM = 0, -1, -2, -3, -4, -5
+INIT = {"FGY": 0, "LBG": 1, "MMX": 2, "DEN": 3, "VAR": 4, "SFF": 5, "KPP": 6, "USER": 7}
+LLOYD_LABELS_IN = 1
+LLOYD_DENSE = 2
+MAX_K = 256
+
+# kq_lloyd_stats, field for field
+STATS_DTYPE = np.dtype([("iters", "<i4"), ("converged", "<i4"), ("k_eff", "<i4"), ("status", "<i4"),
+                        ("ndc", "<i8"), ("sse", "<f8"), ("sse_prev", "<f8")])
+STATS_BYTES = STATS_DTYPE.itemsize  # 40
+
+
+class KqError(RuntimeError):
+    def __init__(self, fn: str, status: int):
+        super().__init__("%s failed: %s (%d)" % (fn, strerror(status), status))
+        self.status = status
+
+
+class SeedParams(C.Structure):
+    _fields_ = [("lbg_eps", C.c_double), ("conv_eps", C.c_double), ("max_iter", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+_lib: Optional[C.CDLL] = None
+_vp = C.c_void_p
+_SIGS = {
+    "kq_workspace_size": (C.c_size_t, [C.c_int64, C.c_int32]),
+    "kq_workspace_init": (C.c_int, [_vp, C.c_size_t, _vp]),
+    "kq_histogram": (C.c_int, [_vp, C.c_int64, _vp, _vp, C.c_int32, _vp, _vp, C.c_size_t, _vp]),
+    "kq_seed": (C.c_int, [_vp, _vp, _vp, C.c_int32, C.c_int32, C.c_uint64, C.POINTER(SeedParams), _vp, _vp,
+                          C.c_size_t, _vp]),
+    "kq_lloyd": (C.c_int, [_vp, _vp, _vp, C.c_int32, _vp, C.c_double, C.c_int32, C.c_uint32, _vp, _vp, _vp, _vp,
+                           _vp, C.c_size_t, _vp]),
+    "kq_map": (C.c_int, [_vp, C.c_int64, _vp, _vp, _vp, _vp, C.c_int32, _vp, _vp, _vp, C.c_size_t, _vp]),
+    "kq_status_read": (C.c_int, [_vp, C.POINTER(C.c_int32), _vp]),
+    "kq_status_clear": (C.c_int, [_vp, _vp]),
+    "kq_strerror": (C.c_char_p, [C.c_int]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib() -> C.CDLL:
+    """Loads libkq.so (building it in-tree if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def strerror(status: int) -> str:
+    return lib().kq_strerror(int(status)).decode()
+
+
+def _ptr(t: Optional[torch.Tensor]) -> Optional[int]:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("libkq takes CUDA tensors (device pointers)")
+    if not t.is_contiguous():
+        raise ValueError("libkq takes contiguous tensors")
+    return t.data_ptr()
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _check(fn: str, st: int) -> int:
+    if st != KQ_OK:
+        raise KqError(fn, st)
+    return st
+
+
+def kq_workspace_size(max_pixels: int, max_K: int = MAX_K) -> int:
+    return int(lib().kq_workspace_size(int(max_pixels), int(max_K)))
+
+
+def kq_workspace_init(ws: torch.Tensor, stream=None) -> None:
+    _check("kq_workspace_init", lib().kq_workspace_init(_ptr(ws), ws.numel() * ws.element_size(), _stream(stream)))
+
+
+def kq_histogram(rgb: torch.Tensor, keys: torch.Tensor, weights: torch.Tensor, n_unique: torch.Tensor,
+                 ws: torch.Tensor, n_pixels: Optional[int] = None, stream=None) -> None:
+    n = rgb.numel() // 3 if n_pixels is None else int(n_pixels)
+    cap = min(keys.numel(), weights.numel())
+    _check("kq_histogram", lib().kq_histogram(_ptr(rgb) if n else None, n, _ptr(keys), _ptr(weights), cap,
+                                              _ptr(n_unique), _ptr(ws), ws.numel() * ws.element_size(),
+                                              _stream(stream)))
+
+
+def kq_seed(keys: torch.Tensor, weights: torch.Tensor, n_unique: torch.Tensor, K: int, scheme, seed: int,
+            centers: torch.Tensor, ws: torch.Tensor, lbg_eps: float = 1.0, conv_eps: float = 1e-4,
+            max_iter: int = 100, stream=None) -> None:
+    sch = INIT[scheme] if isinstance(scheme, str) else int(scheme)
+    p = SeedParams(float(lbg_eps), float(conv_eps), int(max_iter), 0)
+    _check("kq_seed", lib().kq_seed(_ptr(keys), _ptr(weights), _ptr(n_unique), int(K), sch,
+                                    int(seed) & (2**64 - 1), C.byref(p), _ptr(centers), _ptr(ws),
+                                    ws.numel() * ws.element_size(), _stream(stream)))
+
+
+def kq_lloyd(keys: torch.Tensor, weights: torch.Tensor, n_unique: torch.Tensor, K: int, centers: torch.Tensor,
+             eps: float, max_iter: int, labels: torch.Tensor, palette: torch.Tensor, ws: torch.Tensor,
+             stats: Optional[torch.Tensor] = None, sse_hist: Optional[torch.Tensor] = None, flags: int = 0,
+             stream=None) -> None:
+    _check("kq_lloyd", lib().kq_lloyd(_ptr(keys), _ptr(weights), _ptr(n_unique), int(K), _ptr(centers), float(eps),
+                                      int(max_iter), int(flags), _ptr(labels), _ptr(palette), _ptr(stats),
+                                      _ptr(sse_hist), _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)))
+
+
+def kq_map(rgb: torch.Tensor, keys: torch.Tensor, weights: torch.Tensor, n_unique: torch.Tensor,
+           palette: torch.Tensor, K: int, idx: torch.Tensor, ws: torch.Tensor,
+           sse_num: Optional[torch.Tensor] = None, n_pixels: Optional[int] = None, stream=None) -> None:
+    n = rgb.numel() // 3 if n_pixels is None else int(n_pixels)
+    _check("kq_map", lib().kq_map(_ptr(rgb) if n else None, n, _ptr(keys), _ptr(weights), _ptr(n_unique),
+                                  _ptr(palette), int(K), _ptr(idx) if n else None, _ptr(sse_num), _ptr(ws),
+                                  ws.numel() * ws.element_size(), _stream(stream)))
+
+
+def kq_status_read(ws: torch.Tensor, stream=None) -> int:
+    v = C.c_int32(0)
+    _check("kq_status_read", lib().kq_status_read(_ptr(ws), C.byref(v), _stream(stream)))
+    return int(v.value)
+
+
+def kq_status_clear(ws: torch.Tensor, stream=None) -> None:
+    _check("kq_status_clear", lib().kq_status_clear(_ptr(ws), _stream(stream)))
+
+
+def parse_stats(stats: torch.Tensor) -> dict:
+    raw = stats.detach().cpu().numpy().view(np.uint8)[:STATS_BYTES].tobytes()
+    rec = np.frombuffer(raw, dtype=STATS_DTYPE)[0]
+    return {k: rec[k].item() for k in STATS_DTYPE.names}
+
+
+def launches(call: str, n_pixels: int = 1, scheme: str = "KPP", K: int = 1) -> int:
+    """Kernels one call enqueues (the library's own kernels, not memsets)."""
+    if call == "kq_histogram":
+        return 3 if n_pixels > 0 else 2
+    if call == "kq_lloyd":
+        return 1
+    if call == "kq_map":
+        return 2 if n_pixels > 0 else 1
+    if call == "kq_seed":
+        if scheme == "LBG":
+            count, m = 3, 1
+            while m < K:
+                split = m if 2 * m <= K else K - m
+                count += 2 + (1 if split < m else 0)
+                m += split
+            return count
+        return {"FGY": 2, "MMX": 2, "KPP": 2, "SFF": 2, "VAR": 3, "DEN": 4}[scheme]
+    raise ValueError(call)
+
+
+@dataclass
+class Result:
+    idx: torch.Tensor          # palette index per pixel (uint8, device)
+    palette: torch.Tensor      # K x 3 uint8 (device)
+    centers: torch.Tensor      # K x 3 float64 (device)
+    n_unique: torch.Tensor     # device int32 scalar
+    sse_num: torch.Tensor      # device int64 scalar
+    stats: torch.Tensor        # raw kq_lloyd_stats bytes (device)
+
+
+class Quantizer:
+    """Device-resident buffers plus the four calls, for images up to `max_pixels`.
+
+    ``quantize(rgb, K, scheme, seed, eps, max_iter)`` runs histogram, seeding,
+    Weighted Sort-Means and mapping on the current stream with no host
+    synchronisation; read results from the returned device tensors.
+    """
+
+    def __init__(self, max_pixels: int, device=None):
+        dev = torch.device("cuda") if device is None else torch.device(device)
+        self.device = dev
+        self.max_pixels = int(max_pixels)
+        cap = max(1, min(self.max_pixels, 1 << 24))
+        self.capacity = cap
+        nbytes = kq_workspace_size(self.max_pixels, MAX_K)
+        # zero-filled workspace: the library keeps its tables zeroed from here on
+        self.ws = torch.zeros(nbytes, dtype=torch.uint8, device=dev)
+        self.keys = torch.empty(cap, dtype=torch.int32, device=dev)
+        self.weights = torch.empty(cap, dtype=torch.int32, device=dev)
+        self.n_unique = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.labels = torch.zeros(cap, dtype=torch.uint8, device=dev)
+        self.centers = torch.zeros(MAX_K * 3, dtype=torch.float64, device=dev)
+        self.palette = torch.zeros(MAX_K * 3, dtype=torch.uint8, device=dev)
+        self.stats = torch.zeros(64, dtype=torch.uint8, device=dev)
+        self.sse_num = torch.zeros(1, dtype=torch.int64, device=dev)
+        self.idx = torch.empty(max(1, self.max_pixels), dtype=torch.uint8, device=dev)
+        self.launches = 0  # library kernels enqueued so far
+
+    def quantize(self, rgb: torch.Tensor, K: int, scheme: str = "KPP", seed: int = 0, eps: float = 1e-4,
+                 max_iter: int = 100, flags: int = 0, stream=None) -> Result:
+        n = rgb.numel() // 3
+        if n > self.max_pixels:
+            raise ValueError("image larger than this Quantizer's max_pixels")
+        kq_histogram(rgb, self.keys, self.weights, self.n_unique, self.ws, stream=stream)
+        c = self.centers[:3 * K]
+        kq_seed(self.keys, self.weights, self.n_unique, K, scheme, seed, c, self.ws, conv_eps=eps,
+                max_iter=max_iter, stream=stream)
+        pal = self.palette[:3 * K]
+        kq_lloyd(self.keys, self.weights, self.n_unique, K, c, eps, max_iter, self.labels, pal, self.ws,
+                 stats=self.stats, flags=flags, stream=stream)
+        idx = self.idx[:n]
+        kq_map(rgb, self.keys, self.weights, self.n_unique, pal, K, idx, self.ws, sse_num=self.sse_num,
+               stream=stream)
+        self.launches += (launches("kq_histogram", n) + launches("kq_seed", n, scheme, K) + launches("kq_lloyd")
+                          + launches("kq_map", n))
+        return Result(idx=idx, palette=pal.view(K, 3), centers=c.view(K, 3), n_unique=self.n_unique,
+                      sse_num=self.sse_num, stats=self.stats)
+
+
+def exported_symbols() -> list:
+    """Names the header declares (parsed from include/kq.h)."""
+    import re
+
+    hdr = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "kq.h")
+    with open(hdr) as f:
+        text = f.read()
+    return re.findall(r"^KQ_API\s+[\w\s\*]+?\b(kq_\w+)\s*\(", text, flags=re.M)

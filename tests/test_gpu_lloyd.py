@@ -1,0 +1,236 @@
+"""kq_lloyd (Weighted Sort-Means) vs the oracle.
+
+* lockstep: every pass starts from the oracle's centres and previous labels, so
+  the pruned scan runs from the second pass on; labels agree except at oracle
+  near-ties, centres are the oracle's update of the GPU labels, SSE within 1e-5;
+* pruned == full search, bit for bit (the paper's claim that sort-means gives
+  the same result as k-means);
+* free runs: each pass checked against the oracle from the GPU's own state;
+* invariants and degenerate cases.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1101_0395_gb300 import kq, synth
+from tests.gpu_helpers import CENTER_ABS, MSE_REL, Run, check_labels, require_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    require_cuda()
+
+
+def prepared(name, index=0):
+    img = synth.WORKLOADS[name].make(index)
+    r = Run(img)
+    keys, w = r.histogram()
+    return r, keys, w
+
+
+@pytest.fixture(scope="module")
+def plain():
+    return prepared("plain_256")
+
+
+@pytest.fixture(scope="module")
+def paper():
+    return prepared("paper_512")
+
+
+def lockstep(r, keys, w, c0, passes):
+    """Returns the number of tolerated near-tie flips and the last SSEs."""
+    c = np.array(c0, dtype=np.float64)
+    prev = None
+    flips = 0
+    sse_g = sse_o = None
+    for i in range(passes):
+        lab_o, d1, d2, sse_o = oracle.assign(keys, w, c)
+        c_next, sums = oracle.update(keys, w, lab_o, c)
+        g = r.lloyd(c, eps=-1.0, max_iter=1, flags=0 if prev is None else kq.LLOYD_LABELS_IN, labels_in=prev)
+        f = check_labels(keys, c, g["labels"], lab_o, d1, d2)
+        flips += f
+        sse_g = g["stats"]["sse"]
+        assert abs(sse_g - sse_o) <= MSE_REL * max(sse_o, 1.0), (i, sse_g, sse_o)
+        if f == 0:
+            assert np.array_equal(g["centers"], c_next), i
+            assert np.array_equal(g["palette"], oracle.palette(sums, c_next)), i
+        else:
+            c_on_gpu, _ = oracle.update(keys, w, g["labels"], c)
+            assert np.array_equal(g["centers"], c_on_gpu), i
+        assert np.max(np.abs(g["centers"] - c_next)) <= CENTER_ABS or f > 0
+        assert g["stats"]["iters"] == 1
+        prev, c = lab_o, c_next
+    return flips, sse_g, sse_o
+
+
+@pytest.mark.parametrize("scheme", ["KPP", "FGY", "MMX"])
+def test_lockstep_plain(plain, scheme):
+    r, keys, w = plain
+    c0, _ = oracle.seed(keys, w, 16, scheme, 5)
+    lockstep(r, keys, w, c0, 8)
+
+
+@pytest.mark.parametrize("K", [32, 64, 128, 256])
+def test_lockstep_paper_scale(paper, K):
+    r, keys, w = paper
+    c0, _ = oracle.seed(keys, w, K, "KPP", 77 + K)
+    lockstep(r, keys, w, c0, 5)
+
+
+def gpu_trajectory(r, keys, w, c0, eps, max_iter, flags=0):
+    """Free-running GPU passes replayed one at a time (deterministic), each
+    checked against the oracle from the GPU's own centres and labels."""
+    c = np.array(c0, dtype=np.float64)
+    prev = None
+    hist = []
+    flips = 0
+    for i in range(max_iter):
+        lab_o, d1, d2, sse_o = oracle.assign(keys, w, c)
+        g = r.lloyd(c, eps=-1.0, max_iter=1, flags=flags | (0 if prev is None else kq.LLOYD_LABELS_IN),
+                    labels_in=prev)
+        flips += check_labels(keys, c, g["labels"], lab_o, d1, d2)
+        c_on_gpu, _ = oracle.update(keys, w, g["labels"], c)
+        assert np.array_equal(g["centers"], c_on_gpu)
+        assert abs(g["stats"]["sse"] - sse_o) <= MSE_REL * max(sse_o, 1.0)
+        hist.append(g["stats"]["sse"])
+        prev, c = g["labels"], g["centers"]
+        if eps >= 0 and (hist[-1] == 0.0 or (i > 0 and (hist[-2] - hist[-1]) / hist[-1] <= eps)):
+            break
+    return c, prev, np.array(hist), flips
+
+
+@pytest.mark.parametrize("wl,K", [("plain_256", 16), ("paper_512", 256)])
+def test_free_run_matches_stepwise_and_oracle(wl, K, plain, paper):
+    r, keys, w = plain if wl == "plain_256" else paper
+    c0, _ = oracle.seed(keys, w, K, "KPP", 1)
+    free = r.lloyd(c0, eps=1e-4, max_iter=100)
+    c, labels, hist, flips = gpu_trajectory(r, keys, w, c0, 1e-4, 100)
+    # one persistent launch == the same passes issued one by one
+    assert free["stats"]["iters"] == hist.size
+    assert np.array_equal(free["sse_hist"], hist)
+    assert np.array_equal(free["centers"], c) and np.array_equal(free["labels"], labels)
+    assert free["stats"]["converged"] == 1 or hist.size == 100
+    # against the oracle's own free run
+    o = oracle.lloyd(keys, w, c0, 1e-4, 100)
+    if flips == 0 and o["iters"] == hist.size:
+        assert np.array_equal(free["centers"], o["centers"])
+        assert np.array_equal(free["palette"], oracle.palette(o["sums"], o["centers"]))
+        assert abs(hist[-1] - o["sse_hist"][-1]) <= MSE_REL * o["sse_hist"][-1]
+
+
+@pytest.mark.parametrize("wl,K", [("plain_256", 16), ("paper_512", 64), ("paper_512", 256)])
+def test_pruned_equals_dense(wl, K, plain, paper):
+    r, keys, w = plain if wl == "plain_256" else paper
+    c0, _ = oracle.seed(keys, w, K, "FGY", 3)
+    a = r.lloyd(c0, eps=-1.0, max_iter=20)
+    b = r.lloyd(c0, eps=-1.0, max_iter=20, flags=kq.LLOYD_DENSE)
+    assert np.array_equal(a["labels"], b["labels"])
+    assert np.array_equal(a["centers"], b["centers"])
+    assert np.array_equal(a["sse_hist"], b["sse_hist"])
+    n = keys.size
+    assert b["stats"]["ndc"] == K * n * 20
+    assert a["stats"]["ndc"] < b["stats"]["ndc"]
+
+
+def test_invariants(paper):
+    r, keys, w = paper
+    c0, _ = oracle.seed(keys, w, 128, "MMX", 8)
+    g = r.lloyd(c0, eps=1e-4, max_iter=100)
+    h = g["sse_hist"]
+    st = g["stats"]
+    assert np.all(h[1:] <= h[:-1] * (1 + 1e-6))  # FP32 distances: non-increasing up to rounding
+    assert st["iters"] == h.size and st["k_eff"] == 128 and st["status"] == 0
+    if st["converged"]:
+        assert (h[-2] - h[-1]) / h[-1] <= 1e-4
+        assert all((h[i - 1] - h[i]) / h[i] > 1e-4 for i in range(1, h.size - 1))
+    # centres are the weighted means of the last labels, divided in FP64
+    c_ref, sums = oracle.update(keys, w, g["labels"], c0 * 0 + g["centers"])
+    lab = g["labels"]
+    x = oracle.key_to_rgb(keys)
+    for k in np.unique(lab)[:40]:
+        m = lab == k
+        W = int(w[m].astype(np.int64).sum())
+        for ch in range(3):
+            S = int((w[m].astype(np.int64) * x[m, ch]).sum())
+            assert g["centers"][k, ch] == S / W
+    assert np.array_equal(g["palette"], oracle.palette(sums, g["centers"]))
+
+
+def test_k1_and_k_unique():
+    img = synth.image(64, 48, 5, 12.0, 4.0, 31)
+    r = Run(img)
+    keys, w = r.histogram()
+    g = r.lloyd(np.array([[10.0, 20.0, 30.0]]), eps=1e-4, max_iter=10)
+    px = img.reshape(-1, 3).astype(np.int64)
+    assert np.array_equal(g["centers"][0], px.sum(axis=0) / px.shape[0])
+    # pass 1 against the seed, pass 2 against the mean, pass 3 unchanged -> stop
+    assert g["stats"]["iters"] == 3 and g["stats"]["converged"] == 1
+    # every unique colour its own centre: SSE 0 after one pass
+    small = np.array([[5, 5, 5], [9, 9, 9], [5, 5, 5], [200, 1, 2]], dtype=np.uint8)
+    r2 = Run(small)
+    k2, w2 = r2.histogram()
+    c = oracle.key_to_rgb(k2).astype(np.float64)
+    g2 = r2.lloyd(np.vstack([c, c[-1:]]), eps=1e-4, max_iter=10)
+    assert g2["stats"]["sse"] == 0.0 and g2["stats"]["iters"] == 1 and g2["stats"]["k_eff"] == 3
+    assert g2["labels"].tolist() == [0, 1, 2]
+
+
+def test_fixed_iterations_and_single_pass(plain):
+    r, keys, w = plain
+    c0, _ = oracle.seed(keys, w, 16, "KPP", 2)
+    g = r.lloyd(c0, eps=-1.0, max_iter=20)
+    assert g["stats"]["iters"] == 20 and g["stats"]["converged"] == 0
+    g1 = r.lloyd(c0, eps=1e-4, max_iter=1)
+    assert g1["stats"]["iters"] == 1
+
+
+def test_break_boundary_ties():
+    # centres on the red axis at 0, 10, 20; colour (5,0,0) is equidistant from the
+    # first two.  Scanning from centre 1, d(c1, c0) = 100 = 4 * 25 exactly: the
+    # paper's ">=" stop would skip centre 0, but the lowest index must win.
+    img = np.array([[5, 0, 0], [15, 0, 0], [0, 0, 0], [20, 0, 0]], dtype=np.uint8)
+    r = Run(img)
+    keys, w = r.histogram()
+    c = np.array([[0.0, 0, 0], [10.0, 0, 0], [20.0, 0, 0]])
+    labels_in = np.array([0, 1, 1, 2], dtype=np.uint8)  # keys sorted: (0,0,0) (5,0,0) (15,0,0) (20,0,0)
+    g = r.lloyd(c, eps=-1.0, max_iter=1, flags=kq.LLOYD_LABELS_IN, labels_in=labels_in)
+    d = r.lloyd(c, eps=-1.0, max_iter=1, flags=kq.LLOYD_DENSE)
+    assert g["labels"].tolist() == d["labels"].tolist() == [0, 0, 1, 2]
+
+
+def test_coincident_centres_and_bad_labels(plain):
+    r, keys, w = plain
+    c0, _ = oracle.seed(keys, w, 12, "FGY", 4)
+    c0[5] = c0[2]
+    c0[9] = c0[2]
+    bad = np.full(keys.size, 250, dtype=np.uint8)  # out-of-range input labels are treated as 0
+    a = r.lloyd(c0, eps=-1.0, max_iter=6, flags=kq.LLOYD_LABELS_IN, labels_in=bad)
+    b = r.lloyd(c0, eps=-1.0, max_iter=6, flags=kq.LLOYD_DENSE)
+    assert np.array_equal(a["labels"], b["labels"]) and np.array_equal(a["centers"], b["centers"])
+    lockstep(r, keys, w, c0, 3)
+
+
+def test_empty_input():
+    r = Run(np.zeros((0, 3), dtype=np.uint8))
+    r.histogram()
+    g = r.lloyd(np.array([[1.0, 2.0, 3.0], [4.0, 5.0, 6.0]]), eps=1e-4, max_iter=5)
+    assert g["stats"]["iters"] == 1 and g["stats"]["sse"] == 0.0
+    assert g["centers"].tolist() == [[1.0, 2.0, 3.0], [4.0, 5.0, 6.0]]
+    assert g["palette"].tolist() == [[1, 2, 3], [4, 5, 6]]
+
+
+def test_large_image_lockstep():
+    # 4096 x 4096 (16.7 Mpx, ~1.3M unique colours), K = 256: histogram bit-exact,
+    # seeds bit-exact, three lockstep passes
+    img = synth.WORKLOADS["large_4096"].make(0)
+    r = Run(img)
+    keys, w = r.histogram()
+    ok, ow = oracle.histogram(img)
+    assert np.array_equal(keys, ok) and np.array_equal(w, ow)
+    got = r.seed(256, "KPP", 4096)
+    want, _ = oracle.seed(keys, w, 256, "KPP", 4096)
+    assert np.array_equal(got, want)
+    lockstep(r, keys, w, want, 3)

@@ -1,0 +1,87 @@
+"""kq_map vs the oracle: indices and squared-error sums bit-exact."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1101_0395_gb300 import synth
+from tests.gpu_helpers import Run, require_cuda, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    require_cuda()
+
+
+def palette_for(keys, K, seed):
+    rng = np.random.default_rng(seed)
+    return rng.integers(0, 256, size=(K, 3)).astype(np.uint8)
+
+
+@pytest.mark.parametrize("name,K", [("plain_256", 16), ("paper_512", 32), ("paper_512", 256)])
+def test_map_workloads(name, K):
+    img = synth.WORKLOADS[name].make(1)
+    r = Run(img)
+    keys, w = r.histogram()
+    pal = palette_for(keys, K, K)
+    idx, sse = r.map(pal)
+    oidx, osse = oracle.map_pixels(img, pal)
+    assert np.array_equal(idx, oidx) and sse == osse
+
+
+@pytest.mark.parametrize("n", [1, 7, 16, 17, 100, 4099])
+@pytest.mark.parametrize("offset", [0, 1, 5])
+def test_map_ragged_and_misaligned(n, offset):
+    rng = np.random.default_rng(n * 31 + offset)
+    img = rng.integers(0, 256, size=(n, 3), dtype=np.uint8)
+    img[n // 3:] = img[n // 3:] // 16 * 16
+    r = Run(img)
+    keys, w = r.histogram()
+    pal = palette_for(keys, 40, n)
+    buf = torch.zeros(img.size + 64, dtype=torch.uint8, device="cuda")
+    buf[offset:offset + img.size] = to_dev(img.reshape(-1))
+    idx, sse = r.map(pal, rgb=buf[offset:offset + img.size], idx_offset=(offset * 7) % 16)
+    oidx, osse = oracle.map_pixels(img, pal)
+    assert np.array_equal(idx, oidx) and sse == osse
+
+
+def test_map_ties_go_to_lowest_index():
+    img = np.array([[10, 10, 10], [20, 20, 20], [15, 15, 15], [0, 0, 0]] * 10, dtype=np.uint8)
+    pal = np.array([[20, 20, 20], [10, 10, 10], [10, 10, 10], [20, 20, 20]], dtype=np.uint8)
+    r = Run(img)
+    r.histogram()
+    idx, sse = r.map(pal)
+    oidx, osse = oracle.map_pixels(img, pal)
+    assert np.array_equal(idx, oidx) and sse == osse
+    assert idx[:4].tolist() == [1, 0, 0, 1]
+
+
+def test_map_k1_and_k256():
+    img = synth.WORKLOADS["plain_256"].make(3)
+    r = Run(img)
+    keys, w = r.histogram()
+    for K in (1, 256):
+        pal = palette_for(keys, K, 99 + K)
+        idx, sse = r.map(pal)
+        oidx, osse = oracle.map_pixels(img, pal)
+        assert np.array_equal(idx, oidx) and sse == osse
+
+
+def test_map_large_sampled():
+    # 4096 x 4096: every pixel's index checked on a 200k-pixel sample, the error
+    # sum checked exactly through the unique colours
+    img = synth.WORKLOADS["large_4096"].make(0)
+    r = Run(img)
+    keys, w = r.histogram()
+    pal = palette_for(keys, 256, 7)
+    idx, sse = r.map(pal)
+    px = img.reshape(-1, 3)
+    sel = np.random.default_rng(0).choice(px.shape[0], 200_000, replace=False)
+    oidx, _ = oracle.map_pixels(px[sel], pal)
+    assert np.array_equal(idx[sel], oidx)
+    uimg = oracle.key_to_rgb(keys).astype(np.uint8)
+    uidx, _ = oracle.map_pixels(uimg, pal)
+    d = ((oracle.key_to_rgb(keys) - pal[uidx].astype(np.int64)) ** 2).sum(axis=1)
+    assert sse == int((d * w.astype(np.int64)).sum())
