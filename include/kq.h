@@ -180,6 +180,33 @@ KQ_API int kq_map(const uint8_t *rgb, int64_t n_pixels, const uint32_t *keys, co
            const int32_t *n_unique, const uint8_t *palette, int32_t K, uint8_t *idx, int64_t *sse_num, void *ws,
            size_t ws_bytes, kq_stream_t stream);
 
+/*
+ * kq_lloyd without a workspace (the paper has no counterpart: this entry point
+ * exists for callers of this library that cannot allocate device memory -- for
+ * example a plug-in inside a host application that owns the whole device memory
+ * budget and hands the plug-in only its input and output buffers, or code that
+ * must not trigger the device-wide synchronisation of cudaMalloc/cudaFree).
+ *
+ * Same arguments, results and device-side behaviour as kq_lloyd, minus `ws`.
+ * Its scratch (control block, cluster sums, SSE partials and the sorted
+ * centre-distance rows) is one static device array of 356,352 bytes inside
+ * libkq.so; every GPU that loads the library holds it until the process exits.
+ *  - Limit: K <= 256 (the array holds sums and rows for 256 centres); K > 256,
+ *    like any invalid argument, returns KQ_EINVAL.
+ *  - It allocates nothing: no cudaMalloc, no cudaFree, no allocating library call.
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - Every call clears the control block (status, barrier counters) and uses
+ *    the same array: calls that overlap on the GPU (several streams, several
+ *    host threads on one device) race and give wrong results.  Order them.
+ *  - Device-side errors go to stats->status (the array's status word is not
+ *    readable through kq_status_read).
+ */
+KQ_API int kq_lloyd_noalloc(const uint32_t *keys, const uint32_t *weights, const int32_t *n_unique, int32_t K,
+                            double *centers, double eps, int32_t max_iter, uint32_t flags, uint8_t *labels,
+                            uint8_t *palette, kq_lloyd_stats *stats, double *sse_hist, kq_stream_t stream);
+
 /* Device status word of `ws` copied to *h_status (synchronizes `stream`). */
 KQ_API int kq_status_read(const void *ws, int32_t *h_status, kq_stream_t stream);
 

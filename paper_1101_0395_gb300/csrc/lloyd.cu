@@ -19,6 +19,8 @@
 //      and packed as (distance bits with the low 8 cleared) | index, built one row
 //      per block.
 //   -- grid barrier --
+#include <mutex>
+
 #include "kq_dev.cuh"
 
 namespace kq {
@@ -319,4 +321,88 @@ int launch_lloyd(const uint32_t *keys, const uint32_t *w, const int32_t *n_uniqu
     return e == cudaSuccess ? KQ_OK : KQ_ECUDA;
 }
 
+// ---------------------------------------------------------------- allocation-free variant
+// kq_lloyd_noalloc runs the same kernel as kq_lloyd, with its scratch (control
+// block, cluster sums, SSE partials, centre-distance rows) in one file-scope
+// device array instead of a caller-allocated workspace.
+namespace {
+
+constexpr size_t kNoAllocCtl = 0;
+constexpr size_t kNoAllocSums = 4096;
+constexpr size_t kNoAllocSse = kNoAllocSums + sizeof(unsigned long long) * 3 * kMaxK * 4;
+constexpr size_t kNoAllocRows = kNoAllocSse + sizeof(double) * 2 * kMaxGrid;
+constexpr size_t kNoAllocBytes = kNoAllocRows + sizeof(uint32_t) * kMaxK * kMaxK;  // 356,352 bytes
+static_assert(sizeof(Ctl) <= kNoAllocSums, "control block fits its slot");
+
+// Shared by every call on a device and kept for the life of the process.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocDevices = 64;
+void *g_noalloc_ptr[kNoAllocDevices];
+std::mutex g_noalloc_mu;
+
+// Device address of the scratch array on the current device.  The host-side
+// name g_noalloc_scratch is only a stand-in for the symbol; the address comes
+// from cudaGetSymbolAddress, once per device, with that device current.
+int noalloc_scratch(void **out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocDevices) return KQ_ECUDA;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return KQ_ECUDA;
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return KQ_OK;
+}
+
+}  // namespace
 }  // namespace kq
+
+extern "C" KQ_API int kq_lloyd_noalloc(const uint32_t *keys, const uint32_t *weights, const int32_t *n_unique,
+                                       int32_t K, double *centers, double eps, int32_t max_iter, uint32_t flags,
+                                       uint8_t *labels, uint8_t *palette, kq_lloyd_stats *stats, double *sse_hist,
+                                       kq_stream_t stream)
+{
+    using namespace kq;
+    if (!keys || !weights || !n_unique || !centers || !labels || !palette) return KQ_EINVAL;
+    // the scratch array holds sums and distance rows for at most kMaxK (256) centres
+    if (K < 1 || K > kMaxK || max_iter < 1 || eps != eps) return KQ_EINVAL;
+    if (flags & ~(KQ_LLOYD_LABELS_IN | KQ_LLOYD_DENSE)) return KQ_EINVAL;
+    void *base = nullptr;
+    const int st = noalloc_scratch(&base);
+    if (st != KQ_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    char *b = static_cast<char *>(base);
+    // status, abort flag and barrier counters must start at zero; the kernel
+    // clears the sums and the distance count itself
+    if (cudaMemsetAsync(b + kNoAllocCtl, 0, sizeof(Ctl), s) != cudaSuccess) return KQ_ECUDA;
+    const DeviceInfo di = device_info();
+    int per_sm = max_coresident((const void *)lloyd_kernel, kLloydBlock, 0);
+    if (per_sm < 1) return KQ_ECUDA;
+    int grid = di.sms * per_sm;
+    if (grid > kMaxGrid) grid = kMaxGrid;
+    LloydArgs a;
+    a.keys = keys;
+    a.w = weights;
+    a.n_unique = n_unique;
+    a.K = K;
+    a.eps = eps;
+    a.max_iter = max_iter;
+    a.flags = flags;
+    a.skip_if_n_le = 0;
+    a.centers = centers;
+    a.labels = labels;
+    a.palette = palette;
+    a.stats = stats;
+    a.sse_hist = sse_hist;
+    a.ctl = reinterpret_cast<Ctl *>(b + kNoAllocCtl);
+    a.sums = reinterpret_cast<unsigned long long *>(b + kNoAllocSums);
+    a.sse_part = reinterpret_cast<double *>(b + kNoAllocSse);
+    a.rows = reinterpret_cast<uint32_t *>(b + kNoAllocRows);
+    void *args[] = {&a};
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)lloyd_kernel, dim3(grid), dim3(kLloydBlock), args, 0, s);
+    return e == cudaSuccess ? KQ_OK : KQ_ECUDA;
+}

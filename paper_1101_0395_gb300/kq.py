@@ -51,6 +51,8 @@ _SIGS = {
     "kq_lloyd": (C.c_int, [_vp, _vp, _vp, C.c_int32, _vp, C.c_double, C.c_int32, C.c_uint32, _vp, _vp, _vp, _vp,
                            _vp, C.c_size_t, _vp]),
     "kq_map": (C.c_int, [_vp, C.c_int64, _vp, _vp, _vp, _vp, C.c_int32, _vp, _vp, _vp, C.c_size_t, _vp]),
+    "kq_lloyd_noalloc": (C.c_int, [_vp, _vp, _vp, C.c_int32, _vp, C.c_double, C.c_int32, C.c_uint32, _vp, _vp,
+                                   _vp, _vp, _vp]),
     "kq_status_read": (C.c_int, [_vp, C.POINTER(C.c_int32), _vp]),
     "kq_status_clear": (C.c_int, [_vp, _vp]),
     "kq_strerror": (C.c_char_p, [C.c_int]),
@@ -135,6 +137,17 @@ def kq_lloyd(keys: torch.Tensor, weights: torch.Tensor, n_unique: torch.Tensor, 
     _check("kq_lloyd", lib().kq_lloyd(_ptr(keys), _ptr(weights), _ptr(n_unique), int(K), _ptr(centers), float(eps),
                                       int(max_iter), int(flags), _ptr(labels), _ptr(palette), _ptr(stats),
                                       _ptr(sse_hist), _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)))
+
+
+def kq_lloyd_noalloc(keys: torch.Tensor, weights: torch.Tensor, n_unique: torch.Tensor, K: int,
+                     centers: torch.Tensor, eps: float, max_iter: int, labels: torch.Tensor, palette: torch.Tensor,
+                     stats: Optional[torch.Tensor] = None, sse_hist: Optional[torch.Tensor] = None, flags: int = 0,
+                     stream=None) -> None:
+    """kq_lloyd with its scratch in the library's static device array (no workspace)."""
+    _check("kq_lloyd_noalloc", lib().kq_lloyd_noalloc(_ptr(keys), _ptr(weights), _ptr(n_unique), int(K),
+                                                      _ptr(centers), float(eps), int(max_iter), int(flags),
+                                                      _ptr(labels), _ptr(palette), _ptr(stats), _ptr(sse_hist),
+                                                      _stream(stream)))
 
 
 def kq_map(rgb: torch.Tensor, keys: torch.Tensor, weights: torch.Tensor, n_unique: torch.Tensor,

@@ -11,7 +11,7 @@ WS = C.c_void_p(1 << 20)  # aligned fake address: never dereferenced on these pa
 def test_exports_every_declared_symbol():
     names = kq.exported_symbols()
     assert set(names) == {"kq_workspace_size", "kq_workspace_init", "kq_histogram", "kq_seed", "kq_lloyd", "kq_map",
-                          "kq_status_read", "kq_status_clear", "kq_strerror"}
+                          "kq_lloyd_noalloc", "kq_status_read", "kq_status_clear", "kq_strerror"}
     L = kq.lib()
     for n in names:
         assert getattr(L, n) is not None
