@@ -120,8 +120,30 @@ __device__ __forceinline__ uint64_t globaltimer_ns()
     return t;
 }
 
-// Barrier over the first `nblocks` blocks of a cooperative launch.  Every wait is
-// bounded: after kWaitNs, or when another block has given up, it records
+__device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_gpu(uint32_t *p, uint32_t v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Arrival counter that wraps to 0 after `last`: the last arrival resets it.
+__device__ __forceinline__ uint32_t atom_inc_acq_rel_gpu(uint32_t *p, uint32_t last)
+{
+    uint32_t old;
+    asm volatile("atom.acq_rel.gpu.global.inc.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(last) : "memory");
+    return old;
+}
+
+// Barrier over the first `nblocks` blocks of a cooperative launch.  Thread 0 of
+// each block arrives on a self-resetting counter; the last arrival advances the
+// generation with a release store, the others poll it with acquire loads.  Every
+// wait is bounded: after kWaitNs, or when another block has given up, it records
 // KQ_ETIMEOUT, raises `abort` and returns false; the caller then returns.
 __device__ __forceinline__ bool grid_sync(Ctl *ctl, unsigned nblocks)
 {
@@ -129,33 +151,31 @@ __device__ __forceinline__ bool grid_sync(Ctl *ctl, unsigned nblocks)
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        volatile uint32_t *genp = &ctl->bar_gen;
-        volatile uint32_t *abortp = &ctl->abort;
-        uint32_t gen = *genp;
-        __threadfence();
-        if (*abortp) {
+        const uint32_t gen = ld_acquire_gpu(&ctl->bar_gen);
+        if (ld_acquire_gpu(&ctl->abort)) {
             ok = 0;
         } else {
-            uint32_t arrived = atomicAdd(&ctl->bar_count, 1u);
+            __threadfence();  // this block's writes before the arrival
+            const uint32_t arrived = atom_inc_acq_rel_gpu(&ctl->bar_count, nblocks - 1);
             if (arrived == nblocks - 1) {
-                atomicExch(&ctl->bar_count, 0u);
-                __threadfence();
-                atomicAdd(&ctl->bar_gen, 1u);
+                st_release_gpu(&ctl->bar_gen, gen + 1);
             } else {
-                uint64_t t0 = globaltimer_ns();
-                while (*genp == gen) {
-                    if (*abortp) { ok = 0; break; }
-                    if (globaltimer_ns() - t0 > kWaitNs) {
-                        fail(ctl, KQ_ETIMEOUT);
-                        atomicExch(&ctl->abort, 1u);
-                        ok = 0;
-                        break;
+                uint64_t t0 = 0;
+                for (uint32_t spin = 0; ld_acquire_gpu(&ctl->bar_gen) == gen; ++spin) {
+                    if ((spin & 63u) == 63u) {
+                        if (ld_acquire_gpu(&ctl->abort)) { ok = 0; break; }
+                        const uint64_t now = globaltimer_ns();
+                        if (t0 == 0) t0 = now;
+                        else if (now - t0 > kWaitNs) {
+                            fail(ctl, KQ_ETIMEOUT);
+                            atomicExch(&ctl->abort, 1u);
+                            ok = 0;
+                            break;
+                        }
                     }
-                    __nanosleep(40);
                 }
             }
         }
-        __threadfence();
         s_ok = ok;
     }
     __syncthreads();

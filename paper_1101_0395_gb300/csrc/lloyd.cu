@@ -27,7 +27,13 @@ namespace kq {
 namespace {
 
 constexpr int kLloydBlock = 512;
-constexpr int kPtsPerThread = 4;  // blocks used = ceil(N' / (block * this)), capped by the launch
+constexpr int kPtsPerThread = 1;  // blocks used = ceil(N' / (block * this)), capped by the launch
+// Row padding entry: distance bits of a huge finite float, so the scan always stops on it.
+constexpr uint32_t kPadEntry = 0x7F7FFF00u;
+// The first kRowCache entries of every row are copied to shared memory each pass
+// (row stride kRowCache + 1 words, so lanes reading different rows hit different banks).
+constexpr int kRowCache = 32;
+constexpr int kRowStride = kRowCache + 1;
 constexpr float kPruneSlack = 1.0f + 0x1p-17f;
 constexpr unsigned kFull = 0xffffffffu;
 
@@ -48,43 +54,94 @@ struct LloydArgs {
     Ctl *ctl;
     unsigned long long *sums;  // [3][kMaxK][4]: pass i adds into buffer i % 3
     double *sse_part;          // [2][kMaxGrid]
-    uint32_t *rows;            // [K][K]
+    uint32_t *rows;            // [K][Kp], Kp = K rounded up to a multiple of 4
 };
 
 struct LloydShared {
     float4 c[kMaxK];
     double c64[kMaxK * 3];
     unsigned long long sum[kMaxK * 4];
-    uint32_t row[kMaxK];
+    uint32_t sum32[kMaxK * 4];  // used instead of sum when the block's sums fit 32 bits
+    uint32_t row[2][kMaxK];
     double red_d[kLloydBlock / 32];
     unsigned long long red_u[kLloydBlock / 32];
     double sse_i;
+    int narrow;
 };
 
+// Rows p = b, b + G, b + 2G, ... of the sorted centre-distance table; the two
+// halves of the block build two rows at once.  Entry rank = number of smaller
+// packed entries (the index in the low byte makes every entry distinct).
 __device__ __forceinline__ void build_rows(LloydShared &sh, int K, int b, int G, uint32_t *rows)
 {
-    for (int p = b; p < K; p += G) {
-        const float4 cp = sh.c[p];
-        for (int t = threadIdx.x; t < K; t += kLloydBlock) {
-            const float4 ct = sh.c[t];
-            const float d = dist3(cp.x, cp.y, cp.z, ct.x, ct.y, ct.z);
-            sh.row[t] = (__float_as_uint(d) & 0xFFFFFF00u) | (uint32_t)t;
+    constexpr int kHalf = kLloydBlock / 2;  // >= kMaxK
+    const int Kp = (K + 3) & ~3;
+    const int hs = threadIdx.x / kHalf, ht = threadIdx.x % kHalf;
+    for (int m = 0; b + G * m < K; m += 2) {
+        const int p = b + G * (m + hs);
+        const bool act = p < K;
+        if (ht < Kp) {
+            uint32_t v = 0xFFFFFFFFu;
+            if (act && ht < K) {
+                const float4 cp = sh.c[p], ct = sh.c[ht];
+                const float d = dist3(cp.x, cp.y, cp.z, ct.x, ct.y, ct.z);
+                v = (__float_as_uint(d) & 0xFFFFFF00u) | (uint32_t)ht;
+            }
+            sh.row[hs][ht] = v;
         }
         __syncthreads();
-        for (int t = threadIdx.x; t < K; t += kLloydBlock) {
-            const uint32_t v = sh.row[t];
-            int r = 0;
-            for (int u = 0; u < K; ++u) r += (sh.row[u] < v) ? 1 : 0;
-            rows[(size_t)p * K + r] = v;
+        if (act && ht < Kp) {
+            if (ht < K) {
+                const uint32_t v = sh.row[hs][ht];
+                const uint4 *r4 = reinterpret_cast<const uint4 *>(sh.row[hs]);
+                int r = 0;
+#pragma unroll 8
+                for (int u = 0; u < Kp / 4; ++u) {
+                    const uint4 q = r4[u];
+                    r += (q.x < v) + (q.y < v) + (q.z < v) + (q.w < v);
+                }
+                rows[(size_t)p * Kp + r] = v;
+            } else {
+                rows[(size_t)p * Kp + ht] = kPadEntry;
+            }
         }
         __syncthreads();
     }
 }
 
-__device__ __forceinline__ void warp_accumulate(LloydShared &sh, bool active, int arg, uint32_t w, uint32_t key)
+// Adds (w R, w G, w B, w) of each lane's point to its cluster's block sums.  When
+// all lanes of the warp chose the same cluster, one lane adds the warp total.
+// `narrow`: the block's whole slice has sum(w) * 255 < 2^32, so 32-bit sums are
+// exact and the native 32-bit shared-memory atomics can be used.
+__device__ __forceinline__ void warp_accumulate(LloydShared &sh, bool narrow, bool active, int arg, uint32_t w,
+                                                uint32_t key)
 {
     const int a0 = __shfl_sync(kFull, arg, 0);
     const bool same = __all_sync(kFull, !active || arg == a0);
+    if (narrow) {
+        uint32_t W = active ? w : 0u;
+        uint32_t r = W * key_r(key), g = W * key_g(key), bb = W * key_b(key);
+        if (same) {
+            for (int o = 16; o; o >>= 1) {
+                r += __shfl_down_sync(kFull, r, o);
+                g += __shfl_down_sync(kFull, g, o);
+                bb += __shfl_down_sync(kFull, bb, o);
+                W += __shfl_down_sync(kFull, W, o);
+            }
+            if ((threadIdx.x & 31) == 0 && W) {
+                atomicAdd(&sh.sum32[a0 * 4 + 0], r);
+                atomicAdd(&sh.sum32[a0 * 4 + 1], g);
+                atomicAdd(&sh.sum32[a0 * 4 + 2], bb);
+                atomicAdd(&sh.sum32[a0 * 4 + 3], W);
+            }
+        } else if (active) {
+            atomicAdd(&sh.sum32[arg * 4 + 0], r);
+            atomicAdd(&sh.sum32[arg * 4 + 1], g);
+            atomicAdd(&sh.sum32[arg * 4 + 2], bb);
+            atomicAdd(&sh.sum32[arg * 4 + 3], W);
+        }
+        return;
+    }
     unsigned long long W = active ? (unsigned long long)w : 0ull;
     unsigned long long r = W * key_r(key), g = W * key_g(key), bb = W * key_b(key);
     if (same) {
@@ -108,10 +165,12 @@ __device__ __forceinline__ void warp_accumulate(LloydShared &sh, bool active, in
     }
 }
 
-__global__ void __launch_bounds__(kLloydBlock) lloyd_kernel(LloydArgs a)
+__global__ void __launch_bounds__(kLloydBlock, 1) lloyd_kernel(LloydArgs a)
 {
     __shared__ LloydShared sh;
+    extern __shared__ uint32_t row_cache[];  // [K][kRowStride]
     const int K = a.K;
+    const int Kp = (K + 3) & ~3;
     const int64_t n = *a.n_unique;
     if (a.skip_if_n_le > 0 && n <= a.skip_if_n_le) return;
     int64_t want = (n + (int64_t)kLloydBlock * kPtsPerThread - 1) / ((int64_t)kLloydBlock * kPtsPerThread);
@@ -140,14 +199,32 @@ __global__ void __launch_bounds__(kLloydBlock) lloyd_kernel(LloydArgs a)
 
     int64_t lo, hi;
     slice_of(n, b, G, &lo, &hi);
+    {
+        unsigned long long sw = 0ull;
+        for (int64_t i = lo + tid; i < hi; i += kLloydBlock) sw += a.w[i];
+        sw = block_sum_u64<kLloydBlock>(sw, sh.red_u);
+        if (tid == 0) sh.narrow = sw * 255ull < (1ull << 32) ? 1 : 0;
+        __syncthreads();
+    }
+    const bool narrow = sh.narrow != 0;
     double prev_sse = 0.0;
     int it = 0;
     for (;;) {
         const int buf = it & 1;
         unsigned long long *gsum = a.sums + (size_t)(it % 3) * kMaxK * 4;
-        for (int j = tid; j < K * 4; j += kLloydBlock) sh.sum[j] = 0ull;
+        for (int j = tid; j < K * 4; j += kLloydBlock) {
+            sh.sum[j] = 0ull;
+            sh.sum32[j] = 0u;
+        }
         __syncthreads();
         const bool use_prev = prune && (labels_in || it > 0);
+        if (use_prev) {
+            for (int j = tid; j < K * kRowCache; j += kLloydBlock) {
+                const int pr = j / kRowCache, c = j % kRowCache;
+                row_cache[pr * kRowStride + c] = c < Kp ? __ldcg(a.rows + (size_t)pr * Kp + c) : kPadEntry;
+            }
+            __syncthreads();
+        }
         double sse = 0.0;
         unsigned long long ndc = 0ull;
         for (int64_t base = lo; base < hi; base += kLloydBlock) {
@@ -159,52 +236,109 @@ __global__ void __launch_bounds__(kLloydBlock) lloyd_kernel(LloydArgs a)
             if (active) {
                 key = a.keys[i];
                 w = a.w[i];
+            }
+            if (use_prev) {
+                // Sort-means scan from the previous centre p.  Each lane first walks its own
+                // point's row through the shared-memory copy of the first kRowCache entries;
+                // points whose bound has not stopped them by then continue together, the
+                // whole warp testing 32 further entries of that point's row per step.
+                const int lane = tid & 31;
+                int p = active ? a.labels[i] : 0;
+                if (p >= K) p = 0;
                 const float x = (float)key_r(key), y = (float)key_g(key), z = (float)key_b(key);
-                if (use_prev) {
-                    int p = a.labels[i];
-                    if (p >= K) p = 0;
-                    const float4 cp = sh.c[p];
-                    const float prev = dist3(x, y, z, cp.x, cp.y, cp.z);
-                    best = prev;
-                    arg = p;
-                    ++ndc;
-                    const float thr = __fmul_rn(4.0f * prev, kPruneSlack);
-                    const uint32_t *row = a.rows + (size_t)p * K;
-                    for (int j = 0; j < K; ++j) {
-                        const uint32_t e = row[j];
-                        if (__uint_as_float(e & 0xFFFFFF00u) > thr) break;
-                        const int t = (int)(e & 0xFFu);
-                        if (t == p) continue;
-                        const float4 ct = sh.c[t];
-                        const float d = dist3(x, y, z, ct.x, ct.y, ct.z);
-                        ++ndc;
-                        if (d < best || (d == best && t < arg)) {
-                            best = d;
-                            arg = t;
+                const float4 cp = sh.c[p];
+                const float prev = dist3(x, y, z, cp.x, cp.y, cp.z);
+                const float thr = __fmul_rn(4.0f * prev, kPruneSlack);
+                float bd = prev;
+                uint32_t bt = (uint32_t)p;
+                bool done = !active;
+                const uint32_t *rc = row_cache + p * kRowStride;
+                const int jl = Kp < kRowCache ? Kp : kRowCache;
+                for (int j = 0; j < jl; ++j) {
+                    if (!done) {
+                        const uint32_t e = rc[j];
+                        if (__uint_as_float(e & 0xFFFFFF00u) > thr) {
+                            done = true;
+                        } else {
+                            const uint32_t t = e & 0xFFu;
+                            if (t != (uint32_t)p) {
+                                const float4 ct = sh.c[t];
+                                const float d = dist3(x, y, z, ct.x, ct.y, ct.z);
+                                ++ndc;
+                                if (d < bd || (d == bd && t < bt)) {
+                                    bd = d;
+                                    bt = t;
+                                }
+                            }
                         }
                     }
-                } else {
-                    best = __int_as_float(0x7f800000);
-                    for (int k = 0; k < K; ++k) {
-                        const float4 ct = sh.c[k];
-                        const float d = dist3(x, y, z, ct.x, ct.y, ct.z);
-                        if (d < best) {
-                            best = d;
-                            arg = k;
-                        }
-                    }
-                    ndc += (unsigned long long)K;
+                    if ((j & 7) == 7 && !__any_sync(kFull, !done)) break;
                 }
+                unsigned tail = __ballot_sync(kFull, !done && Kp > kRowCache);
+                while (tail) {
+                    const int q = __ffs(tail) - 1;
+                    tail &= tail - 1;
+                    const uint32_t kq = __shfl_sync(kFull, key, q);
+                    const int pq = __shfl_sync(kFull, p, q);
+                    const float thq = __shfl_sync(kFull, thr, q);
+                    float qd = __shfl_sync(kFull, bd, q);
+                    uint32_t qt = __shfl_sync(kFull, bt, q);
+                    const float qx = (float)key_r(kq), qy = (float)key_g(kq), qz = (float)key_b(kq);
+                    const uint32_t *row = a.rows + (size_t)pq * Kp;
+                    for (int j0 = kRowCache; j0 < Kp; j0 += 32) {
+                        const uint32_t e = (j0 + lane < Kp) ? __ldcg(row + j0 + lane) : kPadEntry;
+                        const bool brk = __uint_as_float(e & 0xFFFFFF00u) > thq;
+                        const unsigned bal = __ballot_sync(kFull, brk);
+                        const uint32_t t = e & 0xFFu;
+                        if (!brk && t != (uint32_t)pq) {
+                            const float4 ct = sh.c[t];
+                            const float d = dist3(qx, qy, qz, ct.x, ct.y, ct.z);
+                            ++ndc;
+                            if (d < qd || (d == qd && t < qt)) {
+                                qd = d;
+                                qt = t;
+                            }
+                        }
+                        if (bal) break;
+                    }
+                    const uint32_t md = __reduce_min_sync(kFull, __float_as_uint(qd));
+                    const uint32_t mt = __reduce_min_sync(kFull, __float_as_uint(qd) == md ? qt : 0xFFFFFFFFu);
+                    if (lane == q) {
+                        bd = __uint_as_float(md);
+                        bt = mt;
+                    }
+                }
+                if (active) {
+                    ++ndc;  // the distance to the previous centre
+                    best = bd;
+                    arg = (int)bt;
+                }
+            } else if (active) {
+                const float x = (float)key_r(key), y = (float)key_g(key), z = (float)key_b(key);
+                best = __int_as_float(0x7f800000);
+                for (int k = 0; k < K; ++k) {
+                    const float4 ct = sh.c[k];
+                    const float d = dist3(x, y, z, ct.x, ct.y, ct.z);
+                    if (d < best) {
+                        best = d;
+                        arg = k;
+                    }
+                }
+                ndc += (unsigned long long)K;
+            }
+            if (active) {
                 a.labels[i] = (uint8_t)arg;
                 sse += (double)w * (double)best;
             }
-            warp_accumulate(sh, active, arg, w, key);
+            warp_accumulate(sh, narrow, active, arg, w, key);
         }
         const double bsse = block_sum_f64<kLloydBlock>(sse, sh.red_d);
         const unsigned long long bndc = block_sum_u64<kLloydBlock>(ndc, sh.red_u);
         __syncthreads();
-        for (int j = tid; j < K * 4; j += kLloydBlock)
-            if (sh.sum[j]) atomicAdd(gsum + j, sh.sum[j]);
+        for (int j = tid; j < K * 4; j += kLloydBlock) {
+            const unsigned long long v = narrow ? (unsigned long long)sh.sum32[j] : sh.sum[j];
+            if (v) atomicAdd(gsum + j, v);
+        }
         if (tid == 0) {
             a.sse_part[(size_t)buf * kMaxGrid + b] = bsse;
             atomicAdd(&ctl->ndc, bndc);
@@ -287,6 +421,18 @@ __global__ void __launch_bounds__(kLloydBlock) lloyd_kernel(LloydArgs a)
     }
 }
 
+// Dynamic shared memory: the row cache for the largest K (one size for every
+// launch, so the occupancy query and the cooperative grid are the same for all K).
+size_t lloyd_smem_bytes() { return sizeof(uint32_t) * (size_t)kMaxK * kRowStride; }
+
+int lloyd_smem_attr(size_t bytes)
+{
+    return cudaFuncSetAttribute((const void *)lloyd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) ==
+                   cudaSuccess
+               ? KQ_OK
+               : KQ_ECUDA;
+}
+
 }  // namespace
 
 int launch_lloyd(const uint32_t *keys, const uint32_t *w, const int32_t *n_unique, int K, double *centers, double eps,
@@ -294,7 +440,9 @@ int launch_lloyd(const uint32_t *keys, const uint32_t *w, const int32_t *n_uniqu
                  double *sse_hist, void *ws, const Layout &L, cudaStream_t s, int skip_if_n_le)
 {
     const DeviceInfo di = device_info();
-    int per_sm = max_coresident((const void *)lloyd_kernel, kLloydBlock, 0);
+    const size_t smem = lloyd_smem_bytes();
+    if (lloyd_smem_attr(smem) != KQ_OK) return KQ_ECUDA;
+    int per_sm = max_coresident((const void *)lloyd_kernel, kLloydBlock, smem);
     if (per_sm < 1) return KQ_ECUDA;
     int grid = di.sms * per_sm;
     if (grid > kMaxGrid) grid = kMaxGrid;
@@ -317,7 +465,7 @@ int launch_lloyd(const uint32_t *keys, const uint32_t *w, const int32_t *n_uniqu
     a.sse_part = at<double>(ws, L.l_sse);
     a.rows = at<uint32_t>(ws, L.l_rows);
     void *args[] = {&a};
-    cudaError_t e = cudaLaunchCooperativeKernel((const void *)lloyd_kernel, dim3(grid), dim3(kLloydBlock), args, 0, s);
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)lloyd_kernel, dim3(grid), dim3(kLloydBlock), args, smem, s);
     return e == cudaSuccess ? KQ_OK : KQ_ECUDA;
 }
 
@@ -380,7 +528,9 @@ extern "C" KQ_API int kq_lloyd_noalloc(const uint32_t *keys, const uint32_t *wei
     // clears the sums and the distance count itself
     if (cudaMemsetAsync(b + kNoAllocCtl, 0, sizeof(Ctl), s) != cudaSuccess) return KQ_ECUDA;
     const DeviceInfo di = device_info();
-    int per_sm = max_coresident((const void *)lloyd_kernel, kLloydBlock, 0);
+    const size_t smem = lloyd_smem_bytes();
+    if (lloyd_smem_attr(smem) != KQ_OK) return KQ_ECUDA;
+    int per_sm = max_coresident((const void *)lloyd_kernel, kLloydBlock, smem);
     if (per_sm < 1) return KQ_ECUDA;
     int grid = di.sms * per_sm;
     if (grid > kMaxGrid) grid = kMaxGrid;
@@ -403,6 +553,6 @@ extern "C" KQ_API int kq_lloyd_noalloc(const uint32_t *keys, const uint32_t *wei
     a.sse_part = reinterpret_cast<double *>(b + kNoAllocSse);
     a.rows = reinterpret_cast<uint32_t *>(b + kNoAllocRows);
     void *args[] = {&a};
-    cudaError_t e = cudaLaunchCooperativeKernel((const void *)lloyd_kernel, dim3(grid), dim3(kLloydBlock), args, 0, s);
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)lloyd_kernel, dim3(grid), dim3(kLloydBlock), args, smem, s);
     return e == cudaSuccess ? KQ_OK : KQ_ECUDA;
 }

@@ -201,18 +201,29 @@ struct FarArgs {
 struct FarShared {
     unsigned long long red[kFarBlock / 32];
     unsigned long long scan[kFarBlock / 32];
-    unsigned long long found;
-    uint32_t cur;
-    int gstar;
     unsigned long long resid;
+    int gstar;
+    uint32_t key;
+    int found;
 };
 
-// Sampling by inverse CDF: with total = sum of the G block partials part[] and
-// t = below(u, total), the index of the first item whose running sum of
-// `value` exceeds t.  The block is found from the partials, the item inside that
-// block's slice.  Every block computes the same answer.
-template <typename V>
-__device__ uint32_t locate(FarShared &sh, const unsigned long long *part, int G, int64_t n, uint64_t u, V value)
+constexpr int kFarPer = 4;                    // consecutive colours per thread and chunk
+constexpr int kFarChunk = kFarBlock * kFarPer;
+
+// Minmax candidate: larger D^2 first, then the lower key (keys ascend with the
+// index, so this is the lowest index among ties).
+__device__ __forceinline__ unsigned long long mmx_pack(uint32_t d2, uint32_t key)
+{
+    return ((unsigned long long)d2 << 24) | (unsigned long long)(0xFFFFFFu - key);
+}
+
+// k-means++ sampling by inverse CDF.  With total = sum of the G block partials
+// and t = below(u, total), the sample is the first colour whose running sum of
+// P = w (first round) or w D^2 exceeds t.  Warp 0 finds the block from the
+// partials, then the block scans that block's slice one chunk at a time.
+// Every block computes the same key.
+__device__ uint32_t kpp_locate(const FarArgs &a, FarShared &sh, const unsigned long long *part,
+                               const uint32_t *d2, int G, int64_t n, uint64_t u, bool first_round)
 {
     const int tid = threadIdx.x;
     if (tid < 32) {
@@ -220,12 +231,9 @@ __device__ uint32_t locate(FarShared &sh, const unsigned long long *part, int G,
         for (int g = tid; g < G; g += 32) total += __ldcg(part + g);
         for (int o = 16; o; o >>= 1) total += __shfl_xor_sync(kFull, total, o);
         const unsigned long long t = below(u, total);
-        // first g with prefix(part[0..g]) > t, 32 partials at a time
-        unsigned long long run = 0ull;
+        unsigned long long run = 0ull, resid = 0ull;
         int gstar = G - 1;
-        unsigned long long resid = 0ull;
-        bool done = false;
-        for (int base = 0; base < G && !done; base += 32) {
+        for (int base = 0; base < G; base += 32) {
             const int g = base + tid;
             const unsigned long long v = g < G ? __ldcg(part + g) : 0ull;
             unsigned long long x = v;
@@ -233,55 +241,71 @@ __device__ uint32_t locate(FarShared &sh, const unsigned long long *part, int G,
                 const unsigned long long y = __shfl_up_sync(kFull, x, o);
                 if (tid >= o) x += y;
             }
-            const bool hit = g < G && run + x > t;
-            const unsigned bal = __ballot_sync(kFull, hit);
+            const unsigned bal = __ballot_sync(kFull, g < G && run + x > t);
             if (bal) {
                 const int l = __ffs(bal) - 1;
-                const unsigned long long xl = __shfl_sync(kFull, x, l);
-                const unsigned long long vl = __shfl_sync(kFull, v, l);
                 gstar = base + l;
-                resid = t - (run + xl - vl);
-                done = true;
-            } else {
-                run += __shfl_sync(kFull, x, 31);
+                resid = t - (run + __shfl_sync(kFull, x, l) - __shfl_sync(kFull, v, l));
+                break;
             }
+            run += __shfl_sync(kFull, x, 31);
         }
         if (tid == 0) {
             sh.gstar = gstar;
             sh.resid = resid;
-            sh.found = ~0ull;
+            sh.found = 0;
+            sh.key = 0u;
         }
     }
     __syncthreads();
-    const int gstar = sh.gstar;
     const unsigned long long resid = sh.resid;
     int64_t lo, hi;
-    slice_of(n, gstar, G, &lo, &hi);
+    slice_of(n, sh.gstar, G, &lo, &hi);
     unsigned long long run = 0ull;
-    for (int64_t base = lo; base < hi; base += kFarBlock) {
-        const int64_t i = base + tid;
-        const unsigned long long v = i < hi ? value(i) : 0ull;
+    for (int64_t cb = lo; cb < hi; cb += kFarChunk) {
+        unsigned long long p[kFarPer];
+        uint32_t key[kFarPer];
+        unsigned long long tsum = 0ull;
+#pragma unroll
+        for (int k = 0; k < kFarPer; ++k) {
+            const int64_t i = cb + (int64_t)kFarPer * tid + k;
+            p[k] = 0ull;
+            key[k] = 0u;
+            if (i < hi) {
+                const unsigned long long wi = __ldcg(a.w + i);
+                p[k] = first_round ? wi : wi * (unsigned long long)__ldcg(d2 + i);
+                key[k] = __ldcg(a.keys + i);
+            }
+            tsum += p[k];
+        }
         unsigned long long tot;
-        const unsigned long long ex = block_excl_scan_u64<kFarBlock>(v, sh.scan, &tot);
-        if (i < hi && run + ex <= resid && run + ex + v > resid) sh.found = (unsigned long long)i;
+        const unsigned long long ex = block_excl_scan_u64<kFarBlock>(tsum, sh.scan, &tot);
+        if (run + ex <= resid && resid < run + ex + tsum) {
+            unsigned long long acc = run + ex;
+#pragma unroll
+            for (int k = 0; k < kFarPer; ++k) {
+                if (acc <= resid && resid < acc + p[k]) {
+                    sh.key = key[k];
+                    sh.found = 1;
+                }
+                acc += p[k];
+            }
+        }
         __syncthreads();
-        if (sh.found != ~0ull) break;
+        if (sh.found) break;
         run += tot;
     }
-    __syncthreads();
-    unsigned long long f = sh.found;
-    if (f == ~0ull) f = (unsigned long long)(hi > lo ? hi - 1 : 0);  // unreachable with exact sums
-    return (uint32_t)f;
+    return sh.key;  // a consistent total always finds a colour
 }
 
-__global__ void __launch_bounds__(kFarBlock) seed_far(FarArgs a)
+__global__ void __launch_bounds__(kFarBlock, 1) seed_far(FarArgs a)
 {
     __shared__ FarShared sh;
     const int64_t n = *a.n_unique;
     if (n <= a.K) return;
     const int K = a.K;
-    int64_t want = (n + (int64_t)kFarBlock * 4 - 1) / ((int64_t)kFarBlock * 4);
-    const int G = (int)(want < 1 ? 1 : (want > gridDim.x ? gridDim.x : want));
+    const int64_t want = (n + kFarChunk - 1) / kFarChunk;
+    const int G = (int)(want > gridDim.x ? gridDim.x : want);
     const int b = blockIdx.x;
     if (b >= G) return;
     Ctl *ctl = a.ctl;
@@ -294,36 +318,41 @@ __global__ void __launch_bounds__(kFarBlock) seed_far(FarArgs a)
     slice_of(n, b, G, &lo, &hi);
     if (b == 0)
         for (int k = tid; k < kMaxK; k += kFarBlock) a.slot[k] = 0ull;
-    uint32_t cur;
+    uint32_t ckey;
     if (a.mode == 0) {
         unsigned long long s = 0ull;
         for (int64_t i = lo + tid; i < hi; i += kFarBlock) s += a.w[i];
         s = block_sum_u64<kFarBlock>(s, sh.red);
         if (tid == 0) a.part[b] = s;
         if (!grid_sync(ctl, G)) return;
-        cur = locate(sh, a.part, G, n, rand64(a.seed, 2, 0),
-                     [&](int64_t i) { return (unsigned long long)__ldcg(a.w + i); });
+        ckey = kpp_locate(a, sh, a.part, nullptr, G, n, rand64(a.seed, 2, 0), true);
     } else {
-        if (!grid_sync(ctl, G)) return;
-        cur = (uint32_t)below(rand64(a.seed, 3, 0), (uint64_t)n);
+        if (!grid_sync(ctl, G)) return;  // the argmax slots are clear
+        ckey = __ldg(a.keys + below(rand64(a.seed, 3, 0), (uint64_t)n));
     }
-    if (b == 0 && tid == 0) key_to_centre(a.centers, a.keys[cur]);
+    if (b == 0 && tid == 0) key_to_centre(a.centers, ckey);
     for (int r = 1; r < K; ++r) {
-        const uint32_t ck = __ldcg(a.keys + cur);
         // D^2 alternates between two buffers: other blocks may still be reading this
-        // round's buffer (to locate the sample) while this block starts the next round.
+        // round's values (to locate the sample) while this block starts the next round.
         uint32_t *d2 = a.d2 + (size_t)(r & 1) * (size_t)a.max_unique;
         const uint32_t *d2_prev = a.d2 + (size_t)((r - 1) & 1) * (size_t)a.max_unique;
         unsigned long long acc = 0ull;
-        for (int64_t i = lo + tid; i < hi; i += kFarBlock) {
-            const uint32_t d = key_dist2(a.keys[i], ck);
-            const uint32_t md = (r == 1) ? d : min(d2_prev[i], d);
-            d2[i] = md;
-            if (a.mode == 0) {
-                acc += (unsigned long long)a.w[i] * md;
-            } else {
-                const unsigned long long packed = ((unsigned long long)md << 32) | (0xFFFFFFFFu - (uint32_t)i);
-                acc = packed > acc ? packed : acc;
+        for (int64_t cb = lo; cb < hi; cb += kFarChunk) {
+#pragma unroll
+            for (int k = 0; k < kFarPer; ++k) {
+                const int64_t i = cb + (int64_t)kFarPer * tid + k;
+                if (i < hi) {
+                    const uint32_t key = a.keys[i];
+                    const uint32_t d = key_dist2(key, ckey);
+                    const uint32_t md = (r == 1) ? d : min(d2_prev[i], d);
+                    d2[i] = md;
+                    if (a.mode == 0) {
+                        acc += (unsigned long long)a.w[i] * md;
+                    } else {
+                        const unsigned long long pk = mmx_pack(md, key);
+                        acc = pk > acc ? pk : acc;
+                    }
+                }
             }
         }
         unsigned long long *part = a.part + (size_t)(r & 1) * kMaxGrid;
@@ -332,20 +361,18 @@ __global__ void __launch_bounds__(kFarBlock) seed_far(FarArgs a)
             if (tid == 0) part[b] = s;
         } else {
             for (int o = 16; o; o >>= 1) {
-                const unsigned long long other = __shfl_down_sync(kFull, acc, o);
+                const unsigned long long other = __shfl_xor_sync(kFull, acc, o);
                 acc = other > acc ? other : acc;
             }
             if ((tid & 31) == 0 && acc) atomicMax(a.slot + r, acc);
         }
         if (!grid_sync(ctl, G)) return;
         if (a.mode == 0) {
-            cur = locate(sh, part, G, n, rand64(a.seed, 2, (uint32_t)r), [&](int64_t i) {
-                return (unsigned long long)__ldcg(a.w + i) * (unsigned long long)__ldcg(d2 + i);
-            });
+            ckey = kpp_locate(a, sh, part, d2, G, n, rand64(a.seed, 2, (uint32_t)r), false);
         } else {
-            cur = 0xFFFFFFFFu - (uint32_t)(__ldcg(a.slot + r) & 0xFFFFFFFFull);
+            ckey = 0xFFFFFFu - (uint32_t)(__ldcg(a.slot + r) & 0xFFFFFFull);
         }
-        if (b == 0 && tid == 0) key_to_centre(a.centers + 3 * r, __ldcg(a.keys + cur));
+        if (b == 0 && tid == 0) key_to_centre(a.centers + 3 * r, ckey);
     }
 }
 
