@@ -33,9 +33,9 @@ struct Ctl {
     int64_t n_unique_true;     // N' before clamping to the caller's capacity
     unsigned long long ndc;    // distance calculations of the current kq_lloyd call
     uint32_t pad0[26];
-    uint32_t bar_count;        // grid barrier: arrivals in this generation
+    uint32_t bar_count;        // grid barrier: arrivals since the launch (cleared before each launch)
     uint32_t pad1[31];
-    uint32_t bar_gen;          // grid barrier: generation number
+    uint32_t bar_gen;          // unused
     uint32_t pad2[31];
     // seeding scratch scalars
     unsigned long long var_w;  // sum of weights
@@ -48,7 +48,7 @@ static_assert(sizeof(Ctl) <= 4096, "control block must fit its region");
 // ---------------------------------------------------------------- workspace layout
 struct Layout {
     size_t ctl, hist_cnt, hist_bits, hist_chunk, lut;
-    size_t l_sums, l_sse, l_rows;
+    size_t l_sums, l_sse, l_rows, l_cent;
     size_t s_d2, s_part, s_slot, s_chunk, s_gcnt, s_misc, s_labels, s_centers;
     size_t total;
     int64_t max_unique;
@@ -75,6 +75,7 @@ __host__ __device__ inline Layout layout_for(int64_t max_unique)
     L.l_sums = take(sizeof(unsigned long long) * 3 * kMaxK * 4);
     L.l_sse = take(sizeof(double) * 2 * kMaxGrid);
     L.l_rows = take(sizeof(uint32_t) * kMaxK * kMaxK);
+    L.l_cent = take(sizeof(float4) * kMaxK);
     L.s_part = take(sizeof(unsigned long long) * 2 * kMaxGrid);
     L.s_slot = take(sizeof(unsigned long long) * kMaxK);
     L.s_chunk = take(sizeof(uint32_t) * (size_t)kSeedChunks * 3 * 256);
@@ -132,47 +133,38 @@ __device__ __forceinline__ void st_release_gpu(uint32_t *p, uint32_t v)
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Arrival counter that wraps to 0 after `last`: the last arrival resets it.
-__device__ __forceinline__ uint32_t atom_inc_acq_rel_gpu(uint32_t *p, uint32_t last)
+__device__ __forceinline__ void red_release_add_gpu(uint32_t *p, uint32_t v)
 {
-    uint32_t old;
-    asm volatile("atom.acq_rel.gpu.global.inc.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(last) : "memory");
-    return old;
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Barrier over the first `nblocks` blocks of a cooperative launch.  Thread 0 of
-// each block arrives on a self-resetting counter; the last arrival advances the
-// generation with a release store, the others poll it with acquire loads.  Every
-// wait is bounded: after kWaitNs, or when another block has given up, it records
+// Barrier over the first `nblocks` blocks of a cooperative launch.  The arrival
+// counter starts at 0 (the launcher clears it on the stream before the launch)
+// and only grows: barrier m of the launch is passed once it reaches
+// (m + 1) * nblocks, which the caller tracks in `*epoch`.  Thread 0 of each block
+// arrives with one release reduction and polls with acquire loads.  Every wait is
+// bounded: after kWaitNs, or when another block has given up, it records
 // KQ_ETIMEOUT, raises `abort` and returns false; the caller then returns.
-__device__ __forceinline__ bool grid_sync(Ctl *ctl, unsigned nblocks)
+__device__ __forceinline__ bool grid_sync(Ctl *ctl, unsigned nblocks, uint32_t *epoch)
 {
     __shared__ int s_ok;
+    *epoch += nblocks;
+    const uint32_t target = *epoch;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        const uint32_t gen = ld_acquire_gpu(&ctl->bar_gen);
-        if (ld_acquire_gpu(&ctl->abort)) {
-            ok = 0;
-        } else {
-            __threadfence();  // this block's writes before the arrival
-            const uint32_t arrived = atom_inc_acq_rel_gpu(&ctl->bar_count, nblocks - 1);
-            if (arrived == nblocks - 1) {
-                st_release_gpu(&ctl->bar_gen, gen + 1);
-            } else {
-                uint64_t t0 = 0;
-                for (uint32_t spin = 0; ld_acquire_gpu(&ctl->bar_gen) == gen; ++spin) {
-                    if ((spin & 63u) == 63u) {
-                        if (ld_acquire_gpu(&ctl->abort)) { ok = 0; break; }
-                        const uint64_t now = globaltimer_ns();
-                        if (t0 == 0) t0 = now;
-                        else if (now - t0 > kWaitNs) {
-                            fail(ctl, KQ_ETIMEOUT);
-                            atomicExch(&ctl->abort, 1u);
-                            ok = 0;
-                            break;
-                        }
-                    }
+        red_release_add_gpu(&ctl->bar_count, 1u);
+        uint64_t t0 = 0;
+        for (uint32_t spin = 0; ld_acquire_gpu(&ctl->bar_count) < target; ++spin) {
+            if ((spin & 63u) == 63u) {
+                if (ld_acquire_gpu(&ctl->abort)) { ok = 0; break; }
+                const uint64_t now = globaltimer_ns();
+                if (t0 == 0) t0 = now;
+                else if (now - t0 > kWaitNs) {
+                    fail(ctl, KQ_ETIMEOUT);
+                    atomicExch(&ctl->abort, 1u);
+                    ok = 0;
+                    break;
                 }
             }
         }
@@ -210,11 +202,16 @@ __device__ __forceinline__ float dist3(float x, float y, float z, float cx, floa
     return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
 }
 
-// Exact integer squared distance between two colours.
+// Exact integer squared distance between two colours: with the key bytes as a
+// vector, |a - b|^2 = |a|^2 + |b|^2 - 2 a.b, each dot product one byte-wise dp4a.
+__device__ __forceinline__ uint32_t key_norm2(uint32_t a) { return __dp4a(a, a, 0u); }
+__device__ __forceinline__ uint32_t key_dist2n(uint32_t a, uint32_t na, uint32_t b, uint32_t nb)
+{
+    return na + nb - 2u * __dp4a(a, b, 0u);
+}
 __device__ __forceinline__ uint32_t key_dist2(uint32_t a, uint32_t b)
 {
-    int dr = (int)key_r(a) - (int)key_r(b), dg = (int)key_g(a) - (int)key_g(b), db = (int)key_b(a) - (int)key_b(b);
-    return (uint32_t)(dr * dr + dg * dg + db * db);
+    return key_dist2n(a, key_norm2(a), b, key_norm2(b));
 }
 
 // ---------------------------------------------------------------- block reductions
@@ -245,6 +242,21 @@ __device__ __forceinline__ double block_sum_f64(double v, double *scratch)
     double t = 0.0;
     if (threadIdx.x == 0)
         for (int i = 0; i < BLOCK / 32; ++i) t += scratch[i];
+    return t;  // valid in thread 0
+}
+
+// Fixed-order FP32 block sum (same tree as block_sum_f64); valid in thread 0.
+template <int BLOCK>
+__device__ __forceinline__ float block_sum_f32(float v, float *scratch)
+{
+    for (int o = 16; o; o >>= 1) v = __fadd_rn(v, __shfl_down_sync(0xffffffffu, v, o));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) scratch[warp] = v;
+    __syncthreads();
+    float t = 0.f;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < BLOCK / 32; ++i) t = __fadd_rn(t, scratch[i]);
     return t;  // valid in thread 0
 }
 

@@ -1,24 +1,27 @@
 // lloyd.cu -- Weighted Sort-Means (Algorithm 2) as one persistent cooperative kernel.
 //
 // Every pass runs on the device with no host round trip:
-//   A. assignment: each block owns a contiguous slice of the unique colours (in key
-//      order, so neighbouring threads hold similar colours).  A point starts at its
-//      previous centre p and scans row p of the sorted centre-distance table; the
-//      scan stops at the first centre t with d(c_p, c_t) > 4 d(x, c_p) (1 + 2^-17)
-//      (Section 2.2, item 3: if 2 d(x, c_p) <= d(c_p, c_t) then c_t is no nearer).
-//      The widened bound and a row table rounded down make the stop conservative
-//      under FP32 rounding, so the labels equal a full FP32 search with the lowest
-//      index winning ties.  Each block accumulates exact int64 sums
-//      (w R, w G, w B, w) per cluster in shared memory, its FP64 SSE partial and
-//      its distance count.
+//   A. assignment: the unique colours (in key order) are cut into chunks of 32, and
+//      block b takes chunks b, b + G, b + 2G, ... (neighbouring lanes hold similar
+//      colours; every block samples the whole key range, which evens out the work).
+//      A point starts at its previous centre p and scans row p of the sorted
+//      centre-distance table; the scan stops at the first centre t with
+//      d(c_p, c_t) > 4 d(x, c_p) (1 + 2^-17) (Section 2.2, item 3: if
+//      2 d(x, c_p) <= d(c_p, c_t) then c_t is no nearer).  The widened bound and a
+//      row table rounded down make the stop conservative under FP32 rounding, so the
+//      labels equal a full FP32 search with the lowest index winning ties.  Each
+//      block accumulates exact integer sums (w R, w G, w B, w) per cluster in shared
+//      memory, its FP64 SSE partial and its distance count.
 //   -- grid barrier --
-//   B. update (every block, redundantly and identically): centres = S / W in FP64
-//      (an empty cluster keeps its centre), SSE_i = fixed-order sum of the block
-//      partials, the stopping test of Section 3.3.  Block 0 writes the outputs.
-//   C. table: rows of squared centre-to-centre distances, each sorted ascending
-//      and packed as (distance bits with the low 8 cleared) | index, built one row
-//      per block.
+//   B. update: every block evaluates SSE_i (a fixed-order sum of the block
+//      partials) and the stopping test of Section 3.3 identically; block b divides
+//      the sums of the clusters it owns (k = b, b + G, ...) in FP64 (an empty
+//      cluster keeps its centre) and publishes their FP32 copies.
 //   -- grid barrier --
+//   C. every block loads all FP32 centres; with pruning it builds its rows of the
+//      squared centre-to-centre distance table, each sorted ascending and packed as
+//      (distance bits with the low 8 cleared) | index.
+//   -- grid barrier (pruning only) --
 #include <mutex>
 
 #include "kq_dev.cuh"
@@ -53,8 +56,9 @@ struct LloydArgs {
     double *sse_hist;
     Ctl *ctl;
     unsigned long long *sums;  // [3][kMaxK][4]: pass i adds into buffer i % 3
-    double *sse_part;          // [2][kMaxGrid]
+    float *sse_part;           // [2][kMaxGrid] block SSE partials (FP32, fixed-order trees)
     uint32_t *rows;            // [K][Kp], Kp = K rounded up to a multiple of 4
+    float4 *cent;              // [K] FP32 centres published by their owner blocks
 };
 
 struct LloydShared {
@@ -63,9 +67,10 @@ struct LloydShared {
     unsigned long long sum[kMaxK * 4];
     uint32_t sum32[kMaxK * 4];  // used instead of sum when the block's sums fit 32 bits
     uint32_t row[2][kMaxK];
-    double red_d[kLloydBlock / 32];
+    float red_f[kLloydBlock / 32];
     unsigned long long red_u[kLloydBlock / 32];
     double sse_i;
+    int conv;
     int narrow;
 };
 
@@ -178,9 +183,12 @@ __global__ void __launch_bounds__(kLloydBlock, 1) lloyd_kernel(LloydArgs a)
     const int b = blockIdx.x;
     if (b >= G) return;
     Ctl *ctl = a.ctl;
-    const int tid = threadIdx.x;
+    uint32_t bar_epoch = 0;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int kWarps = kLloydBlock / 32;
     const bool prune = !(a.flags & KQ_LLOYD_DENSE);
     const bool labels_in = (a.flags & KQ_LLOYD_LABELS_IN) != 0;
+    const int64_t nch = (n + 31) / 32;  // 32-colour chunks; this block takes b, b + G, ...
 
     for (int k = tid; k < K; k += kLloydBlock) {
         const double x = a.centers[3 * k], y = a.centers[3 * k + 1], z = a.centers[3 * k + 2];
@@ -189,47 +197,55 @@ __global__ void __launch_bounds__(kLloydBlock, 1) lloyd_kernel(LloydArgs a)
         sh.c64[3 * k + 2] = z;
         sh.c[k] = make_float4((float)x, (float)y, (float)z, 0.f);
     }
-    __syncthreads();
-    if (prune) build_rows(sh, K, b, G, a.rows);
-    if (b == 0) {
-        for (int j = tid; j < 3 * kMaxK * 4; j += kLloydBlock) a.sums[j] = 0ull;
-        if (tid == 0) ctl->ndc = 0ull;
-    }
-    if (!grid_sync(ctl, G)) return;
-
-    int64_t lo, hi;
-    slice_of(n, b, G, &lo, &hi);
     {
         unsigned long long sw = 0ull;
-        for (int64_t i = lo + tid; i < hi; i += kLloydBlock) sw += a.w[i];
+        for (int64_t c = b + (int64_t)G * warp; c < nch; c += (int64_t)G * kWarps) {
+            const int64_t i = c * 32 + lane;
+            if (i < n) sw += a.w[i];
+        }
         sw = block_sum_u64<kLloydBlock>(sw, sh.red_u);
         if (tid == 0) sh.narrow = sw * 255ull < (1ull << 32) ? 1 : 0;
         __syncthreads();
     }
     const bool narrow = sh.narrow != 0;
+    if (prune) build_rows(sh, K, b, G, a.rows);
+    if (b == 0) {
+        for (int j = tid; j < 3 * kMaxK * 4; j += kLloydBlock) a.sums[j] = 0ull;
+        if (tid == 0) ctl->ndc = 0ull;
+    }
+    if (!grid_sync(ctl, G, &bar_epoch)) return;
+
     double prev_sse = 0.0;
     int it = 0;
     for (;;) {
+        // ---- A: assignment
         const int buf = it & 1;
         unsigned long long *gsum = a.sums + (size_t)(it % 3) * kMaxK * 4;
         for (int j = tid; j < K * 4; j += kLloydBlock) {
             sh.sum[j] = 0ull;
             sh.sum32[j] = 0u;
         }
-        __syncthreads();
         const bool use_prev = prune && (labels_in || it > 0);
         if (use_prev) {
-            for (int j = tid; j < K * kRowCache; j += kLloydBlock) {
-                const int pr = j / kRowCache, c = j % kRowCache;
-                row_cache[pr * kRowStride + c] = c < Kp ? __ldcg(a.rows + (size_t)pr * Kp + c) : kPadEntry;
+            // the first kRowCache entries of every row, 16 bytes per load
+            constexpr int kQ = kRowCache / 4;
+            for (int j = tid; j < K * kQ; j += kLloydBlock) {
+                const int pr = j / kQ, q4 = j % kQ;
+                uint4 v = make_uint4(kPadEntry, kPadEntry, kPadEntry, kPadEntry);
+                if (4 * q4 < Kp) v = __ldcg(reinterpret_cast<const uint4 *>(a.rows + (size_t)pr * Kp) + q4);
+                uint32_t *dst = row_cache + pr * kRowStride + 4 * q4;
+                dst[0] = v.x;
+                dst[1] = v.y;
+                dst[2] = v.z;
+                dst[3] = v.w;
             }
-            __syncthreads();
         }
-        double sse = 0.0;
+        __syncthreads();
+        float sse32 = 0.f;
         unsigned long long ndc = 0ull;
-        for (int64_t base = lo; base < hi; base += kLloydBlock) {
-            const int64_t i = base + tid;
-            const bool active = i < hi;
+        for (int64_t c = b + (int64_t)G * warp; c < nch; c += (int64_t)G * kWarps) {
+            const int64_t i = c * 32 + lane;
+            const bool active = i < n;
             uint32_t key = 0u, w = 0u;
             int arg = 0;
             float best = 0.f;
@@ -242,7 +258,6 @@ __global__ void __launch_bounds__(kLloydBlock, 1) lloyd_kernel(LloydArgs a)
                 // point's row through the shared-memory copy of the first kRowCache entries;
                 // points whose bound has not stopped them by then continue together, the
                 // whole warp testing 32 further entries of that point's row per step.
-                const int lane = tid & 31;
                 int p = active ? a.labels[i] : 0;
                 if (p >= K) p = 0;
                 const float x = (float)key_r(key), y = (float)key_g(key), z = (float)key_b(key);
@@ -328,11 +343,12 @@ __global__ void __launch_bounds__(kLloydBlock, 1) lloyd_kernel(LloydArgs a)
             }
             if (active) {
                 a.labels[i] = (uint8_t)arg;
-                sse += (double)w * (double)best;
+                // w < 2^32 and best are FP32; one rounding per product, FP64 above the thread
+                sse32 = __fadd_rn(sse32, __fmul_rn((float)w, best));
             }
             warp_accumulate(sh, narrow, active, arg, w, key);
         }
-        const double bsse = block_sum_f64<kLloydBlock>(sse, sh.red_d);
+        const float bsse = block_sum_f32<kLloydBlock>(sse32, sh.red_f);
         const unsigned long long bndc = block_sum_u64<kLloydBlock>(ndc, sh.red_u);
         __syncthreads();
         for (int j = tid; j < K * 4; j += kLloydBlock) {
@@ -343,80 +359,86 @@ __global__ void __launch_bounds__(kLloydBlock, 1) lloyd_kernel(LloydArgs a)
             a.sse_part[(size_t)buf * kMaxGrid + b] = bsse;
             atomicAdd(&ctl->ndc, bndc);
         }
-        if (!grid_sync(ctl, G)) return;
+        if (!grid_sync(ctl, G, &bar_epoch)) return;
 
-        // ---- B: update and stopping test (identical in every block)
+        // ---- B: SSE, stopping test, owned centres.  FP64 instructions are slow on
+        // this GPU, so the stopping test (warp 0) and the three channel divisions of
+        // the owned clusters (warps 1-3) run in different warps.
         ++it;
-        if (tid < 32) {
-            double s = 0.0;
-            for (int g = tid; g < G; g += 32) s += __ldcg(a.sse_part + (size_t)buf * kMaxGrid + g);
-            for (int o = 16; o; o >>= 1) s += __shfl_down_sync(kFull, s, o);
-            if (tid == 0) sh.sse_i = s;
-        }
-        for (int k = tid; k < K; k += kLloydBlock) {
-            const unsigned long long W = __ldcg(gsum + 4 * k + 3);
-            if (W) {
-                const double dw = (double)W;
-                const double x = (double)__ldcg(gsum + 4 * k) / dw;
-                const double y = (double)__ldcg(gsum + 4 * k + 1) / dw;
-                const double z = (double)__ldcg(gsum + 4 * k + 2) / dw;
-                sh.c64[3 * k] = x;
-                sh.c64[3 * k + 1] = y;
-                sh.c64[3 * k + 2] = z;
-                sh.c[k] = make_float4((float)x, (float)y, (float)z, 0.f);
+        if (warp == 0) {
+            float s = 0.f;
+            for (int g = lane; g < G; g += 32) s = __fadd_rn(s, __ldcg(a.sse_part + (size_t)buf * kMaxGrid + g));
+            for (int o = 16; o; o >>= 1) s = __fadd_rn(s, __shfl_down_sync(kFull, s, o));
+            if (lane == 0) {
+                const double si = (double)s;
+                bool conv = false;
+                if (a.eps >= 0.0) {
+                    if (si == 0.0) conv = true;
+                    else if (it > 1 && (prev_sse - si) / si <= a.eps) conv = true;
+                }
+                sh.sse_i = si;
+                sh.conv = conv ? 1 : 0;
+            }
+        } else if (warp <= 3) {
+            const int ch = warp - 1;
+            for (int k = b + G * lane; k < K; k += G * 32) {
+                const unsigned long long W = __ldcg(gsum + 4 * k + 3);
+                if (W) sh.c64[3 * k + ch] = (double)__ldcg(gsum + 4 * k + ch) / (double)W;
             }
         }
         __syncthreads();
         const double sse_i = sh.sse_i;
-        bool conv = false;
-        if (a.eps >= 0.0) {
-            if (sse_i == 0.0) conv = true;
-            else if (it > 1 && (prev_sse - sse_i) / sse_i <= a.eps) conv = true;
-        }
+        const bool conv = sh.conv != 0;
         const bool stop = conv || it >= a.max_iter;
+        for (int k = b + G * tid; k < K; k += G * kLloydBlock) {
+            const unsigned long long W = __ldcg(gsum + 4 * k + 3);
+            const double x = sh.c64[3 * k], y = sh.c64[3 * k + 1], z = sh.c64[3 * k + 2];
+            a.cent[k] = make_float4((float)x, (float)y, (float)z, 0.f);
+            if (stop) {
+                a.centers[3 * k] = x;
+                a.centers[3 * k + 1] = y;
+                a.centers[3 * k + 2] = z;
+                for (int ch = 0; ch < 3; ++ch) {
+                    int v;
+                    if (W) {
+                        const unsigned long long S = __ldcg(gsum + 4 * k + ch);
+                        v = (int)((2ull * S + W) / (2ull * W));
+                    } else {
+                        const double f = floor(sh.c64[3 * k + ch] + 0.5);
+                        v = f < 0.0 ? 0 : (f > 255.0 ? 255 : (int)f);
+                    }
+                    a.palette[3 * k + ch] = (uint8_t)v;
+                }
+            }
+        }
         if (b == 0) {
-            // Buffer (pass + 1) % 3 was read by every block in the previous pass, which
-            // all blocks finished before the barrier above, and is next added into two
-            // passes from now, after a barrier this block must reach first.  (The next
-            // pass's buffer was cleared one pass ago: without pruning there is no
-            // barrier between this update and the next pass's additions.)
+            // Buffer (pass + 1) % 3 was last read in the previous pass and is next added
+            // into two passes from now, after barriers this block must reach first.
             unsigned long long *ahead = a.sums + (size_t)((it + 1) % 3) * kMaxK * 4;
             for (int j = tid; j < kMaxK * 4; j += kLloydBlock) ahead[j] = 0ull;
             if (tid == 0 && a.sse_hist) a.sse_hist[it - 1] = sse_i;
-            if (stop) {
-                for (int j = tid; j < 3 * K; j += kLloydBlock) a.centers[j] = sh.c64[j];
-                for (int k = tid; k < K; k += kLloydBlock) {
-                    const unsigned long long W = __ldcg(gsum + 4 * k + 3);
-                    for (int ch = 0; ch < 3; ++ch) {
-                        int v;
-                        if (W) {
-                            const unsigned long long S = __ldcg(gsum + 4 * k + ch);
-                            v = (int)((2ull * S + W) / (2ull * W));
-                        } else {
-                            const double f = floor(sh.c64[3 * k + ch] + 0.5);
-                            v = f < 0.0 ? 0 : (f > 255.0 ? 255 : (int)f);
-                        }
-                        a.palette[3 * k + ch] = (uint8_t)v;
-                    }
-                }
-                if (tid == 0 && a.stats) {
-                    kq_lloyd_stats st;
-                    st.iters = it;
-                    st.converged = conv ? 1 : 0;
-                    st.k_eff = (int32_t)(n < K ? n : K);
-                    st.status = *(volatile int32_t *)&ctl->status;
-                    st.ndc = (int64_t)*(volatile unsigned long long *)&ctl->ndc;
-                    st.sse = sse_i;
-                    st.sse_prev = it > 1 ? prev_sse : 0.0;
-                    *a.stats = st;
-                }
+            if (stop && tid == 0 && a.stats) {
+                kq_lloyd_stats st;
+                st.iters = it;
+                st.converged = conv ? 1 : 0;
+                st.k_eff = (int32_t)(n < K ? n : K);
+                st.status = *(volatile int32_t *)&ctl->status;
+                st.ndc = (int64_t)*(volatile unsigned long long *)&ctl->ndc;
+                st.sse = sse_i;
+                st.sse_prev = it > 1 ? prev_sse : 0.0;
+                *a.stats = st;
             }
         }
         if (stop) return;
         prev_sse = sse_i;
+        if (!grid_sync(ctl, G, &bar_epoch)) return;
+
+        // ---- C: all centres, then this block's rows of the distance table
+        for (int k = tid; k < K; k += kLloydBlock) sh.c[k] = __ldcg(a.cent + k);
+        __syncthreads();
         if (prune) {
             build_rows(sh, K, b, G, a.rows);
-            if (!grid_sync(ctl, G)) return;
+            if (!grid_sync(ctl, G, &bar_epoch)) return;
         }
     }
 }
@@ -462,8 +484,11 @@ int launch_lloyd(const uint32_t *keys, const uint32_t *w, const int32_t *n_uniqu
     a.sse_hist = sse_hist;
     a.ctl = at<Ctl>(ws, L.ctl);
     a.sums = at<unsigned long long>(ws, L.l_sums);
-    a.sse_part = at<double>(ws, L.l_sse);
+    a.sse_part = at<float>(ws, L.l_sse);
     a.rows = at<uint32_t>(ws, L.l_rows);
+    a.cent = at<float4>(ws, L.l_cent);
+    // the grid barrier's arrival counter starts every launch at zero
+    if (cudaMemsetAsync(&a.ctl->bar_count, 0, sizeof(uint32_t), s) != cudaSuccess) return KQ_ECUDA;
     void *args[] = {&a};
     cudaError_t e = cudaLaunchCooperativeKernel((const void *)lloyd_kernel, dim3(grid), dim3(kLloydBlock), args, smem, s);
     return e == cudaSuccess ? KQ_OK : KQ_ECUDA;
@@ -471,15 +496,16 @@ int launch_lloyd(const uint32_t *keys, const uint32_t *w, const int32_t *n_uniqu
 
 // ---------------------------------------------------------------- allocation-free variant
 // kq_lloyd_noalloc runs the same kernel as kq_lloyd, with its scratch (control
-// block, cluster sums, SSE partials, centre-distance rows) in one file-scope
-// device array instead of a caller-allocated workspace.
+// block, cluster sums, SSE partials, centre-distance rows, published centres) in
+// one file-scope device array instead of a caller-allocated workspace.
 namespace {
 
 constexpr size_t kNoAllocCtl = 0;
 constexpr size_t kNoAllocSums = 4096;
 constexpr size_t kNoAllocSse = kNoAllocSums + sizeof(unsigned long long) * 3 * kMaxK * 4;
 constexpr size_t kNoAllocRows = kNoAllocSse + sizeof(double) * 2 * kMaxGrid;
-constexpr size_t kNoAllocBytes = kNoAllocRows + sizeof(uint32_t) * kMaxK * kMaxK;  // 356,352 bytes
+constexpr size_t kNoAllocCent = kNoAllocRows + sizeof(uint32_t) * kMaxK * kMaxK;
+constexpr size_t kNoAllocBytes = kNoAllocCent + sizeof(float4) * kMaxK;  // 360,448 bytes
 static_assert(sizeof(Ctl) <= kNoAllocSums, "control block fits its slot");
 
 // Shared by every call on a device and kept for the life of the process.
@@ -550,8 +576,9 @@ extern "C" KQ_API int kq_lloyd_noalloc(const uint32_t *keys, const uint32_t *wei
     a.sse_hist = sse_hist;
     a.ctl = reinterpret_cast<Ctl *>(b + kNoAllocCtl);
     a.sums = reinterpret_cast<unsigned long long *>(b + kNoAllocSums);
-    a.sse_part = reinterpret_cast<double *>(b + kNoAllocSse);
+    a.sse_part = reinterpret_cast<float *>(b + kNoAllocSse);
     a.rows = reinterpret_cast<uint32_t *>(b + kNoAllocRows);
+    a.cent = reinterpret_cast<float4 *>(b + kNoAllocCent);
     void *args[] = {&a};
     cudaError_t e = cudaLaunchCooperativeKernel((const void *)lloyd_kernel, dim3(grid), dim3(kLloydBlock), args, smem, s);
     return e == cudaSuccess ? KQ_OK : KQ_ECUDA;

@@ -196,6 +196,7 @@ struct FarArgs {
     uint32_t *d2;              // [2][max_unique]
     unsigned long long *part;  // [2][kMaxGrid]
     unsigned long long *slot;  // [kMaxK]
+    int64_t cluster_cap;       // N' served by seed_far_cluster (0 when it is not used)
 };
 
 struct FarShared {
@@ -302,13 +303,14 @@ __global__ void __launch_bounds__(kFarBlock, 1) seed_far(FarArgs a)
 {
     __shared__ FarShared sh;
     const int64_t n = *a.n_unique;
-    if (n <= a.K) return;
+    if (n <= a.K || n <= a.cluster_cap) return;  // the cluster kernel serves N' <= cluster_cap
     const int K = a.K;
     const int64_t want = (n + kFarChunk - 1) / kFarChunk;
     const int G = (int)(want > gridDim.x ? gridDim.x : want);
     const int b = blockIdx.x;
     if (b >= G) return;
     Ctl *ctl = a.ctl;
+    uint32_t bar_epoch = 0;
     if (n > a.max_unique) {
         if (b == 0 && threadIdx.x == 0) fail(ctl, KQ_ENOMEM);
         return;
@@ -324,10 +326,10 @@ __global__ void __launch_bounds__(kFarBlock, 1) seed_far(FarArgs a)
         for (int64_t i = lo + tid; i < hi; i += kFarBlock) s += a.w[i];
         s = block_sum_u64<kFarBlock>(s, sh.red);
         if (tid == 0) a.part[b] = s;
-        if (!grid_sync(ctl, G)) return;
+        if (!grid_sync(ctl, G, &bar_epoch)) return;
         ckey = kpp_locate(a, sh, a.part, nullptr, G, n, rand64(a.seed, 2, 0), true);
     } else {
-        if (!grid_sync(ctl, G)) return;  // the argmax slots are clear
+        if (!grid_sync(ctl, G, &bar_epoch)) return;  // the argmax slots are clear
         ckey = __ldg(a.keys + below(rand64(a.seed, 3, 0), (uint64_t)n));
     }
     if (b == 0 && tid == 0) key_to_centre(a.centers, ckey);
@@ -366,7 +368,7 @@ __global__ void __launch_bounds__(kFarBlock, 1) seed_far(FarArgs a)
             }
             if ((tid & 31) == 0 && acc) atomicMax(a.slot + r, acc);
         }
-        if (!grid_sync(ctl, G)) return;
+        if (!grid_sync(ctl, G, &bar_epoch)) return;
         if (a.mode == 0) {
             ckey = kpp_locate(a, sh, part, d2, G, n, rand64(a.seed, 2, (uint32_t)r), false);
         } else {
@@ -374,6 +376,224 @@ __global__ void __launch_bounds__(kFarBlock, 1) seed_far(FarArgs a)
         }
         if (b == 0 && tid == 0) key_to_centre(a.centers + 3 * r, ckey);
     }
+}
+
+// ---------------------------------------------------------------- KPP / MMX in one cluster
+// For N' up to kClusterCtas * kClPer colours, one thread-block cluster runs every
+// round.  Each CTA keeps its slice (keys, weights, D^2 in two buffers) in shared
+// memory; per round it writes the inclusive prefix sums of its threads' w D^2
+// (k-means++) or its packed maximum (minmax), passes one hardware cluster barrier,
+// and then reads what it needs from the other CTAs' shared memory (DSMEM): the
+// CTA totals, a 32-ary search over the chosen CTA's thread prefixes and that
+// thread's colours.  Every CTA computes the same next centre.  Buffers alternate
+// by round, so a CTA that starts the next round never overwrites what another CTA
+// may still be reading.
+constexpr int kClBlock = 1024;
+constexpr int kClElems = 12;                       // colours per thread
+constexpr int kClPer = kClBlock * kClElems;        // colours per CTA (12288)
+
+struct ClusterArgs {
+    const uint32_t *keys;
+    const uint32_t *w;
+    const int32_t *n_unique;
+    int K;
+    int mode;       // 0 = k-means++, 1 = minmax
+    int ctas;       // cluster size
+    uint64_t seed;
+    double *centers;
+};
+
+struct ClusterShared {
+    unsigned long long tpre[2][kClBlock];       // warp-local inclusive prefix of thread sums (k-means++)
+    // every CTA's warp totals / maxima, pushed by their owners; rows padded to 33 so
+    // that lane l reading slots 16 l .. 16 l + 15 does not hit one bank
+    unsigned long long wtot[2][16][kClBlock / 32 + 1];
+    uint32_t key;
+};
+
+__device__ __forceinline__ uint32_t cluster_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_sync_all()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t dsmem_addr(const void *local, uint32_t rank)
+{
+    uint32_t out;
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(local);
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(out) : "r"(a), "r"(rank));
+    return out;
+}
+
+__device__ __forceinline__ unsigned long long dsmem_ld64(uint32_t addr)
+{
+    unsigned long long v;
+    asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(addr) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ uint32_t dsmem_ld32(uint32_t addr)
+{
+    uint32_t v;
+    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void dsmem_st64(uint32_t addr, unsigned long long v)
+{
+    asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(addr), "l"(v) : "memory");
+}
+
+__global__ void __launch_bounds__(kClBlock, 1) seed_far_cluster(ClusterArgs a)
+{
+    __shared__ ClusterShared sh;
+    extern __shared__ uint32_t cl_smem[];  // key[kClPer], w[kClPer], d2[2][kClPer]
+    uint32_t *s_key = cl_smem, *s_w = cl_smem + kClPer, *s_d2 = cl_smem + 2 * kClPer;
+    const int64_t n = *a.n_unique;
+    const int C = a.ctas;
+    // this kernel serves K < N' <= C * kClPer; seed_far serves larger N'
+    if (n <= a.K || n > (int64_t)C * kClPer) return;
+    const int K = a.K, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t rank = cluster_rank();
+    const int64_t per = (n + C - 1) / C;
+    const int64_t lo = (int64_t)rank * per < n ? (int64_t)rank * per : n;
+    const int cnt = (int)((lo + per < n ? lo + per : n) - lo);
+    const int ept = (cnt + kClBlock - 1) / kClBlock;  // colours per thread, thread t owns [t ept, t ept + ept)
+    for (int j = tid; j < kClPer; j += kClBlock) {
+        s_key[j] = j < cnt ? a.keys[lo + j] : 0u;
+        s_w[j] = j < cnt ? a.w[lo + j] : 0u;
+    }
+    __syncthreads();
+    uint32_t ckey = 0u, cnorm = 0u;
+    for (int r = 0; r < K; ++r) {
+        const int buf = r & 1;
+        uint32_t *d2 = s_d2 + buf * kClPer;
+        const uint32_t *d2p = s_d2 + (buf ^ 1) * kClPer;
+        unsigned long long acc = 0ull;
+        if (r > 0 || a.mode == 0) {
+#pragma unroll 4
+            for (int k = 0; k < ept; ++k) {
+                const int j = tid * ept + k;
+                if (j < cnt) {
+                    if (r == 0) {
+                        acc += s_w[j];  // k-means++ first centre: probability w / sum w
+                    } else {
+                        const uint32_t key = s_key[j];
+                        const uint32_t d = key_dist2n(key, key_norm2(key), ckey, cnorm);
+                        const uint32_t md = r == 1 ? d : min(d2p[j], d);
+                        d2[j] = md;
+                        if (a.mode == 0) {
+                            acc += (unsigned long long)s_w[j] * md;
+                        } else {
+                            const unsigned long long pk = mmx_pack(md, key);
+                            acc = pk > acc ? pk : acc;
+                        }
+                    }
+                }
+            }
+        }
+        // warp scan (k-means++) or warp maximum (minmax); the warp's total is pushed
+        // into slot [rank][warp] of every CTA of the cluster
+        unsigned long long wv;
+        if (a.mode == 0) {
+            unsigned long long x = acc;
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(kFull, x, o);
+                if (lane >= o) x += y;
+            }
+            sh.tpre[buf][tid] = x;
+            wv = __shfl_sync(kFull, x, 31);
+        } else {
+            for (int o = 16; o; o >>= 1) {
+                const unsigned long long other = __shfl_xor_sync(kFull, acc, o);
+                acc = other > acc ? other : acc;
+            }
+            wv = acc;
+        }
+        if (lane < C) dsmem_st64(dsmem_addr(&sh.wtot[buf][rank][warp], lane), wv);
+        const uint64_t u = a.mode == 0 ? rand64(a.seed, 2, (uint32_t)r) : rand64(a.seed, 3, 0);
+        cluster_sync_all();
+        // Warp 0 of every CTA finds the next centre (reads only this round's buffers,
+        // which nobody writes before the next cluster barrier) and shares it.
+        uint32_t next = 0u;
+        if (warp != 0) {
+        } else if (a.mode == 1) {
+            if (r == 0) {
+                next = a.keys[below(u, (uint64_t)n)];
+            } else {
+                unsigned long long m = 0ull;
+                if (lane < C)
+                    for (int q = 0; q < kClBlock / 32; ++q) m = sh.wtot[buf][lane][q] > m ? sh.wtot[buf][lane][q] : m;
+                for (int o = 16; o; o >>= 1) {
+                    const unsigned long long other = __shfl_xor_sync(kFull, m, o);
+                    m = other > m ? other : m;
+                }
+                next = 0xFFFFFFu - (uint32_t)(m & 0xFFFFFFull);
+            }
+        } else {
+            // CTA totals (lane c sums CTA c's 32 warp totals), then the sampled CTA
+            unsigned long long ct = 0ull;
+            if (lane < C)
+                for (int q = 0; q < kClBlock / 32; ++q) ct += sh.wtot[buf][lane][q];
+            unsigned long long x = ct;
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(kFull, x, o);
+                if (lane >= o) x += y;
+            }
+            const unsigned long long t = below(u, __shfl_sync(kFull, x, 31));
+            const int g = __ffs(__ballot_sync(kFull, lane < C && x > t)) - 1;
+            const unsigned long long r1 = t - (__shfl_sync(kFull, x, g) - __shfl_sync(kFull, ct, g));
+            // the warp of CTA g
+            const unsigned long long wt = sh.wtot[buf][g][lane];
+            unsigned long long xw = wt;
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(kFull, xw, o);
+                if (lane >= o) xw += y;
+            }
+            const int ws = __ffs(__ballot_sync(kFull, xw > r1)) - 1;
+            const unsigned long long resid = r1 - (__shfl_sync(kFull, xw, ws) - __shfl_sync(kFull, wt, ws));
+            // the thread: warp-local inclusive prefixes, read from CTA g
+            const unsigned long long s2 = dsmem_ld64(dsmem_addr(&sh.tpre[buf][ws * 32 + lane], g));
+            const int l2 = __ffs(__ballot_sync(kFull, s2 > resid)) - 1;
+            const unsigned long long prior = l2 > 0 ? __shfl_sync(kFull, s2, l2 - 1) : 0ull;
+            const int ts = ws * 32 + l2;
+            const unsigned long long r2 = resid - prior;
+            // that thread's colours (CTA g's slice and colours per thread)
+            const int64_t glo = (int64_t)g * per;
+            const int gcnt = (int)((glo + per < n ? glo + per : n) - glo);
+            const int gept = (gcnt + kClBlock - 1) / kClBlock;
+            unsigned long long pk = 0ull;
+            uint32_t kk = 0u;
+            if (lane < gept) {
+                const int j = ts * gept + lane;
+                if (j < gcnt) {
+                    kk = dsmem_ld32(dsmem_addr(&s_key[j], g));
+                    const unsigned long long wj = dsmem_ld32(dsmem_addr(&s_w[j], g));
+                    pk = r == 0 ? wj : wj * (unsigned long long)dsmem_ld32(dsmem_addr(&d2[j], g));
+                }
+            }
+            unsigned long long xe = pk;
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(kFull, xe, o);
+                if (lane >= o) xe += y;
+            }
+            const int l3 = __ffs(__ballot_sync(kFull, lane < gept && xe > r2)) - 1;
+            next = __shfl_sync(kFull, kk, l3 < 0 ? 0 : l3);
+        }
+        if (tid == 0) sh.key = next;
+        __syncthreads();
+        ckey = sh.key;
+        cnorm = key_norm2(ckey);
+        if (rank == 0 && tid == 0) key_to_centre(a.centers + 3 * r, ckey);
+    }
+    // no CTA may leave while another can still read its shared memory
+    cluster_sync_all();
 }
 
 // ---------------------------------------------------------------- chunked counts (VAR, DEN)
@@ -697,6 +917,46 @@ __global__ void seed_lbg_split(const int32_t *n_unique, int K, int m, double eps
     }
 }
 
+constexpr size_t kClSmem = sizeof(uint32_t) * 4 * (size_t)kClPer;  // keys, weights, 2 x D^2
+
+// Largest cluster (16, else 8) of seed_far_cluster this device can run, or 0.
+int far_cluster_size()
+{
+    static int cached[64];
+    static bool done[64];
+    const int dev = device_info().device;
+    if (done[dev]) return cached[dev];
+    int best = 0;
+    if (cudaFuncSetAttribute((const void *)seed_far_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kClSmem) == cudaSuccess &&
+        cudaFuncSetAttribute((const void *)seed_far_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+            cudaSuccess) {
+        for (int c : {16, 8}) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(c);
+            cfg.blockDim = dim3(kClBlock);
+            cfg.dynamicSmemBytes = kClSmem;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = c;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            int clusters = 0;
+            if (cudaOccupancyMaxActiveClusters(&clusters, (const void *)seed_far_cluster, &cfg) == cudaSuccess &&
+                clusters >= 1) {
+                best = c;
+                break;
+            }
+        }
+    }
+    cudaGetLastError();  // a refused size is not an error of this call
+    cached[dev] = best;
+    done[dev] = true;
+    return best;
+}
+
 template <typename KFn>
 int set_smem(KFn kernel, size_t bytes)
 {
@@ -734,6 +994,31 @@ int launch_seed(const uint32_t *keys, const uint32_t *w, const int32_t *n_unique
     case KQ_INIT_KPP:
     case KQ_INIT_MMX: {
         const DeviceInfo di = device_info();
+        const int ctas = far_cluster_size();
+        if (ctas > 0) {
+            ClusterArgs ca;
+            ca.keys = keys;
+            ca.w = w;
+            ca.n_unique = n_unique;
+            ca.K = K;
+            ca.mode = scheme == KQ_INIT_KPP ? 0 : 1;
+            ca.ctas = ctas;
+            ca.seed = seed;
+            ca.centers = centers;
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(ctas);
+            cfg.blockDim = dim3(kClBlock);
+            cfg.dynamicSmemBytes = kClSmem;
+            cfg.stream = s;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = ctas;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            if (cudaLaunchKernelEx(&cfg, seed_far_cluster, ca) != cudaSuccess) return KQ_ECUDA;
+        }
         const int per_sm = max_coresident((const void *)seed_far, kFarBlock, 0);
         if (per_sm < 1) return KQ_ECUDA;
         int grid = di.sms * per_sm;
@@ -751,6 +1036,8 @@ int launch_seed(const uint32_t *keys, const uint32_t *w, const int32_t *n_unique
         a.d2 = at<uint32_t>(ws, L.s_d2);
         a.part = at<unsigned long long>(ws, L.s_part);
         a.slot = at<unsigned long long>(ws, L.s_slot);
+        a.cluster_cap = (int64_t)ctas * kClPer;
+        if (cudaMemsetAsync(&ctl->bar_count, 0, sizeof(uint32_t), s) != cudaSuccess) return KQ_ECUDA;
         void *args[] = {&a};
         if (cudaLaunchCooperativeKernel((const void *)seed_far, dim3(grid), dim3(kFarBlock), args, 0, s) != cudaSuccess)
             return KQ_ECUDA;

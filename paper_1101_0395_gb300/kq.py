@@ -191,7 +191,7 @@ def launches(call: str, n_pixels: int = 1, scheme: str = "KPP", K: int = 1) -> i
                 count += 2 + (1 if split < m else 0)
                 m += split
             return count
-        return {"FGY": 2, "MMX": 2, "KPP": 2, "SFF": 2, "VAR": 3, "DEN": 4}[scheme]
+        return {"FGY": 2, "MMX": 3, "KPP": 3, "SFF": 2, "VAR": 3, "DEN": 4}[scheme]
     raise ValueError(call)
 
 

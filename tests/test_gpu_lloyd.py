@@ -141,7 +141,7 @@ def test_invariants(paper):
     g = r.lloyd(c0, eps=1e-4, max_iter=100)
     h = g["sse_hist"]
     st = g["stats"]
-    assert np.all(h[1:] <= h[:-1] * (1 + 1e-6))  # FP32 distances: non-increasing up to rounding
+    assert np.all(h[1:] <= h[:-1] * (1 + 5e-6))  # FP32 distances and FP32 partial sums: non-increasing up to rounding
     assert st["iters"] == h.size and st["k_eff"] == 128 and st["status"] == 0
     if st["converged"]:
         assert (h[-2] - h[-1]) / h[-1] <= 1e-4
