@@ -7,10 +7,11 @@
 //   1. hist_count   streams the packed pixels (three 16-byte loads per 16 pixels),
 //                   adds one to cnt[key] and, on the first touch of a colour,
 //                   sets its presence bit;
-//   2. hist_chunks  counts set bits per 2048-word chunk of the bitmap;
-//   3. hist_emit    turns the bitmap into ascending keys: each block offsets its
-//                   chunk by the counts before it, scans its words, writes keys
-//                   and counts, and zeroes the counters and bits it read.
+//   2. hist_chunks  counts set bits per 256-word chunk of the bitmap (8192 colours)
+//                   and hist_bases turns the counts into each chunk's first output;
+//   3. hist_emit    turns the bitmap into ascending keys: each block writes its
+//                   chunk's keys and counts by output rank, zeroing the counters
+//                   and bits it read.
 // Pixels are read once; the tables are touched only at the colours present.
 #include "kq_dev.cuh"
 
@@ -19,7 +20,9 @@ namespace {
 
 constexpr int kCountBlock = 256;
 constexpr int kEmitBlock = 256;
-static_assert(kHistChunkWords == kEmitBlock * 8, "eight bitmap words per emitting thread");
+static_assert(kHistChunkWords == kEmitBlock, "one bitmap word per emitting thread");
+constexpr int kBaseBlock = 1024;
+static_assert(kHistChunks == 2 * kBaseBlock, "two chunk totals per scanning thread");
 
 __device__ __forceinline__ void add_colour(uint32_t *cnt, uint32_t *bits, uint32_t key)
 {
@@ -75,73 +78,115 @@ __global__ void __launch_bounds__(kCountBlock) hist_count(const uint8_t *__restr
     for (int64_t gi = tid; gi < ngroups; gi += nth) {
         const uint4 a = __ldcs(g + 3 * gi), b = __ldcs(g + 3 * gi + 1), c = __ldcs(g + 3 * gi + 2);
         const uint32_t w[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
-        Unroll16<0>::run(w, [&](uint32_t key) { add_colour(cnt, bits, key); });
+        // all sixteen counter updates go out before any returned value is looked at,
+        // so they overlap; then the first touches set their presence bits
+        uint32_t key[16], old[16];
+        int q = 0;
+        Unroll16<0>::run(w, [&](uint32_t k) { key[q++] = k; });
+#pragma unroll
+        for (int i = 0; i < 16; ++i) old[i] = atomicAdd(cnt + key[i], 1u);
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+            if (old[i] == 0u) atomicOr(bits + (key[i] >> 5), 1u << (key[i] & 31u));
     }
 }
 
 __global__ void __launch_bounds__(kEmitBlock) hist_chunks(const uint32_t *__restrict__ bits, uint32_t *__restrict__ chunk_tot)
 {
     __shared__ unsigned long long s_red[kEmitBlock / 32];
-    const uint4 *p = reinterpret_cast<const uint4 *>(bits + (size_t)blockIdx.x * kHistChunkWords) + 2 * threadIdx.x;
-    const uint4 a = p[0], b = p[1];
-    unsigned long long c = __popc(a.x) + __popc(a.y) + __popc(a.z) + __popc(a.w) + __popc(b.x) + __popc(b.y) +
-                           __popc(b.z) + __popc(b.w);
-    unsigned long long t = block_sum_u64<kEmitBlock>(c, s_red);
+    const unsigned long long c = __popc(bits[(size_t)blockIdx.x * kHistChunkWords + threadIdx.x]);
+    const unsigned long long t = block_sum_u64<kEmitBlock>(c, s_red);
     if (threadIdx.x == 0) chunk_tot[blockIdx.x] = (uint32_t)t;
 }
 
-__global__ void __launch_bounds__(kEmitBlock) hist_emit(uint32_t *__restrict__ bits, uint32_t *__restrict__ cnt,
-                                                        const uint32_t *__restrict__ chunk_tot,
-                                                        uint32_t *__restrict__ keys, uint32_t *__restrict__ weights,
-                                                        int32_t cap, int32_t *__restrict__ n_unique, Ctl *ctl)
+// Exclusive prefix of the chunk totals (each chunk's first output position), the
+// number of colours, and the capacity check.
+__global__ void __launch_bounds__(kBaseBlock) hist_bases(const uint32_t *__restrict__ chunk_tot,
+                                                         uint32_t *__restrict__ chunk_base, int32_t cap,
+                                                         int32_t *__restrict__ n_unique, Ctl *ctl)
 {
-    __shared__ uint32_t s_scan[kEmitBlock / 32];
-    __shared__ uint32_t s_base;
-    const int chunk = blockIdx.x;
-    // offset of this chunk = colours in all chunks before it
-    if (threadIdx.x < 32) {
-        uint32_t s = 0;
-        for (int c = threadIdx.x; c < chunk; c += 32) s += chunk_tot[c];
-        for (int o = 16; o; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if (threadIdx.x == 0) s_base = s;
-    }
-    const size_t w0 = (size_t)chunk * kHistChunkWords + (size_t)threadIdx.x * 8;
-    uint4 *p = reinterpret_cast<uint4 *>(bits + w0);
-    const uint4 a = p[0], b = p[1];
-    const uint32_t wv[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-    uint32_t pc = 0;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) pc += __popc(wv[k]);
+    __shared__ uint32_t s_scan[kBaseBlock / 32];
+    const uint32_t a = chunk_tot[2 * threadIdx.x], b = chunk_tot[2 * threadIdx.x + 1];
     uint32_t tot;
-    const uint32_t excl = block_excl_scan_u32<kEmitBlock>(pc, s_scan, &tot);
+    const uint32_t ex = block_excl_scan_u32<kBaseBlock>(a + b, s_scan, &tot);
+    chunk_base[2 * threadIdx.x] = ex;
+    chunk_base[2 * threadIdx.x + 1] = ex + a;
+    if (threadIdx.x == 0) {
+        ctl->n_unique_true = tot;
+        *n_unique = (int32_t)(tot < (uint32_t)cap ? tot : (uint32_t)cap);
+        if (tot > (uint32_t)cap) fail(ctl, KQ_ECAPACITY);
+    }
+}
+
+// Position of the k-th (0-based) set bit of v, by halving with population counts.
+__device__ __forceinline__ uint32_t select_bit(uint32_t v, int k)
+{
+    uint32_t pos = 0;
+    int c = __popc(v & 0xFFFFu);
+    if (k >= c) { k -= c; v >>= 16; pos += 16; }
+    c = __popc(v & 0xFFu);
+    if (k >= c) { k -= c; v >>= 8; pos += 8; }
+    c = __popc(v & 0xFu);
+    if (k >= c) { k -= c; v >>= 4; pos += 4; }
+    c = __popc(v & 0x3u);
+    if (k >= c) { k -= c; v >>= 2; pos += 2; }
+    if (k >= (int)(v & 1u)) pos += 1;
+    return pos;
+}
+
+// Output by rank: a chunk's colours occupy positions [base, base + total) of the
+// result; thread t writes positions base + t, base + t + 256, ...  The word holding
+// the r-th set bit of the chunk is found by binary search over the per-word prefix
+// counts, the bit itself by select_bit.  Threads get equal shares however unevenly
+// the colours fall in the key space, four counter reads are in flight per thread,
+// and the writes of keys and weights are coalesced.
+__global__ void __launch_bounds__(kEmitBlock) hist_emit(uint32_t *__restrict__ bits, uint32_t *__restrict__ cnt,
+                                                        const uint32_t *__restrict__ chunk_base,
+                                                        uint32_t *__restrict__ keys, uint32_t *__restrict__ weights,
+                                                        int32_t cap)
+{
+    __shared__ uint32_t s_pre[kHistChunkWords];  // exclusive prefix of set bits per word
+    __shared__ uint32_t s_word[kHistChunkWords];
+    __shared__ uint32_t s_scan[kEmitBlock / 32];
+    const int chunk = blockIdx.x;
+    const size_t wi = (size_t)chunk * kHistChunkWords + threadIdx.x;
+    const uint32_t v = bits[wi];
+    uint32_t tot;
+    const uint32_t ex = block_excl_scan_u32<kEmitBlock>(__popc(v), s_scan, &tot);
+    s_word[threadIdx.x] = v;
+    s_pre[threadIdx.x] = ex;
+    if (v) bits[wi] = 0u;
     __syncthreads();
-    int64_t pos = (int64_t)s_base + excl;
+    const int64_t base = chunk_base[chunk];
+    constexpr int kBatch = 4;
+    for (uint32_t r0 = threadIdx.x; r0 < tot; r0 += kEmitBlock * kBatch) {
+        uint32_t key[kBatch], c[kBatch];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        uint32_t m = wv[k];
-        const uint32_t kbase = (uint32_t)(w0 + k) << 5;
-        while (m) {
-            const uint32_t bit = __ffs(m) - 1;
-            m &= m - 1;
-            const uint32_t key = kbase | bit;
-            const uint32_t c = cnt[key];
-            cnt[key] = 0u;
-            if (pos < cap) {
-                keys[pos] = key;
-                weights[pos] = c;
+        for (int j = 0; j < kBatch; ++j) {
+            const uint32_t r = r0 + (uint32_t)j * kEmitBlock;
+            key[j] = 0xFFFFFFFFu;
+            if (r < tot) {
+                int lo = 0, hi = kHistChunkWords - 1;  // last word whose prefix is <= r
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (s_pre[mid] <= r) lo = mid;
+                    else hi = mid - 1;
+                }
+                key[j] = ((uint32_t)(chunk * kHistChunkWords + lo) << 5) | select_bit(s_word[lo], (int)(r - s_pre[lo]));
             }
-            ++pos;
         }
-    }
-    if (pc) {
-        p[0] = make_uint4(0, 0, 0, 0);
-        p[1] = make_uint4(0, 0, 0, 0);
-    }
-    if (chunk == kHistChunks - 1 && threadIdx.x == kEmitBlock - 1) {
-        // pos is now the total number of colours
-        ctl->n_unique_true = pos;
-        *n_unique = (int32_t)(pos < cap ? pos : cap);
-        if (pos > cap) fail(ctl, KQ_ECAPACITY);
+#pragma unroll
+        for (int j = 0; j < kBatch; ++j) c[j] = key[j] != 0xFFFFFFFFu ? cnt[key[j]] : 0u;
+#pragma unroll
+        for (int j = 0; j < kBatch; ++j) {
+            if (key[j] == 0xFFFFFFFFu) continue;
+            cnt[key[j]] = 0u;
+            const int64_t pos = base + r0 + (uint32_t)j * kEmitBlock;
+            if (pos < cap) {
+                keys[pos] = key[j];
+                weights[pos] = c[j];
+            }
+        }
     }
 }
 
@@ -164,8 +209,10 @@ int launch_histogram(const uint8_t *rgb, int64_t n, uint32_t *keys, uint32_t *we
     int grid = (int)(want < (int64_t)di.sms * 8 ? want : (int64_t)di.sms * 8);
     if (grid < 1) grid = 1;
     if (n > 0) hist_count<<<grid, kCountBlock, 0, s>>>(rgb, n, head, cnt, bits);
+    uint32_t *chunk_base = chunk_tot + kHistChunks;
     hist_chunks<<<kHistChunks, kEmitBlock, 0, s>>>(bits, chunk_tot);
-    hist_emit<<<kHistChunks, kEmitBlock, 0, s>>>(bits, cnt, chunk_tot, keys, weights, cap, n_unique, ctl);
+    hist_bases<<<1, kBaseBlock, 0, s>>>(chunk_tot, chunk_base, cap, n_unique, ctl);
+    hist_emit<<<kHistChunks, kEmitBlock, 0, s>>>(bits, cnt, chunk_base, keys, weights, cap);
     return cudaGetLastError() == cudaSuccess ? KQ_OK : KQ_ECUDA;
 }
 

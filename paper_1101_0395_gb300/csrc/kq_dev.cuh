@@ -17,8 +17,8 @@ constexpr int kMaxK = 256;                 // palette indices are uint8_t
 constexpr int kKeyBits = 24;               // (R << 16) | (G << 8) | B
 constexpr int64_t kKeySpace = int64_t(1) << kKeyBits;
 constexpr int kBitWords = 1 << (kKeyBits - 5);   // presence bitmap, one bit per colour
-constexpr int kHistChunkWords = 2048;            // bitmap words per compaction block
-constexpr int kHistChunks = kBitWords / kHistChunkWords;  // 256
+constexpr int kHistChunkWords = 256;             // bitmap words per compaction block (8192 colours)
+constexpr int kHistChunks = kBitWords / kHistChunkWords;  // 2048
 constexpr int kMaxGrid = 4096;             // upper bound on persistent grid sizes
 constexpr int kSeedChunks = 512;           // chunks of the unique list for VAR / DEN lookups
 constexpr int kDenCells = 64;              // 4 levels per channel
@@ -70,7 +70,7 @@ __host__ __device__ inline Layout layout_for(int64_t max_unique)
     L.ctl = take(4096);
     L.hist_cnt = take(sizeof(uint32_t) * (size_t)kKeySpace);
     L.hist_bits = take(sizeof(uint32_t) * (size_t)kBitWords);
-    L.hist_chunk = take(sizeof(uint32_t) * (size_t)kHistChunks);
+    L.hist_chunk = take(sizeof(uint32_t) * 2 * (size_t)kHistChunks);  // totals, then bases
     L.lut = take((size_t)kKeySpace);
     L.l_sums = take(sizeof(unsigned long long) * 3 * kMaxK * 4);
     L.l_sse = take(sizeof(double) * 2 * kMaxGrid);

@@ -63,6 +63,7 @@ struct LloydArgs {
 
 struct LloydShared {
     float4 c[kMaxK];
+    float cx[kMaxK], cy[kMaxK], cz[kMaxK];  // the same FP32 centres, one array per channel
     double c64[kMaxK * 3];
     unsigned long long sum[kMaxK * 4];
     uint32_t sum32[kMaxK * 4];  // used instead of sum when the block's sums fit 32 bits
@@ -111,6 +112,50 @@ __device__ __forceinline__ void build_rows(LloydShared &sh, int K, int b, int G,
             }
         }
         __syncthreads();
+    }
+}
+
+__device__ __forceinline__ void set_centre(LloydShared &sh, int k, float4 c)
+{
+    sh.c[k] = c;
+    sh.cx[k] = c.x;
+    sh.cy[k] = c.y;
+    sh.cz[k] = c.z;
+}
+
+// Full search over all K centres with the lowest index winning ties.  Distances are
+// taken eight at a time and folded with fminf; the running best moves only on a
+// strictly smaller group minimum (so the earliest group holding the minimum wins),
+// and the winning group is evaluated again to find its first centre at that
+// distance.  The same dist3 values as a one-at-a-time scan, so the same argmin.
+__device__ __forceinline__ void dense_argmin(const LloydShared &sh, int K, float x, float y, float z, float &best,
+                                             int &arg)
+{
+    best = __int_as_float(0x7f800000);
+    int bg = -1;
+    int k0 = 0;
+    for (; k0 + 8 <= K; k0 += 8) {
+        float d[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) d[j] = dist3(x, y, z, sh.cx[k0 + j], sh.cy[k0 + j], sh.cz[k0 + j]);
+        const float m = fminf(fminf(fminf(d[0], d[1]), fminf(d[2], d[3])), fminf(fminf(d[4], d[5]), fminf(d[6], d[7])));
+        if (m < best) {
+            best = m;
+            bg = k0;
+        }
+    }
+    arg = 0;
+    if (bg >= 0) {
+#pragma unroll
+        for (int j = 7; j >= 0; --j)
+            if (dist3(x, y, z, sh.cx[bg + j], sh.cy[bg + j], sh.cz[bg + j]) == best) arg = bg + j;
+    }
+    for (int k = k0; k < K; ++k) {
+        const float d = dist3(x, y, z, sh.cx[k], sh.cy[k], sh.cz[k]);
+        if (d < best) {
+            best = d;
+            arg = k;
+        }
     }
 }
 
@@ -195,7 +240,7 @@ __global__ void __launch_bounds__(kLloydBlock, 1) lloyd_kernel(LloydArgs a)
         sh.c64[3 * k] = x;
         sh.c64[3 * k + 1] = y;
         sh.c64[3 * k + 2] = z;
-        sh.c[k] = make_float4((float)x, (float)y, (float)z, 0.f);
+        set_centre(sh, k, make_float4((float)x, (float)y, (float)z, 0.f));
     }
     {
         unsigned long long sw = 0ull;
@@ -329,16 +374,7 @@ __global__ void __launch_bounds__(kLloydBlock, 1) lloyd_kernel(LloydArgs a)
                     arg = (int)bt;
                 }
             } else if (active) {
-                const float x = (float)key_r(key), y = (float)key_g(key), z = (float)key_b(key);
-                best = __int_as_float(0x7f800000);
-                for (int k = 0; k < K; ++k) {
-                    const float4 ct = sh.c[k];
-                    const float d = dist3(x, y, z, ct.x, ct.y, ct.z);
-                    if (d < best) {
-                        best = d;
-                        arg = k;
-                    }
-                }
+                dense_argmin(sh, K, (float)key_r(key), (float)key_g(key), (float)key_b(key), best, arg);
                 ndc += (unsigned long long)K;
             }
             if (active) {
@@ -434,7 +470,7 @@ __global__ void __launch_bounds__(kLloydBlock, 1) lloyd_kernel(LloydArgs a)
         if (!grid_sync(ctl, G, &bar_epoch)) return;
 
         // ---- C: all centres, then this block's rows of the distance table
-        for (int k = tid; k < K; k += kLloydBlock) sh.c[k] = __ldcg(a.cent + k);
+        for (int k = tid; k < K; k += kLloydBlock) set_centre(sh, k, __ldcg(a.cent + k));
         __syncthreads();
         if (prune) {
             build_rows(sh, K, b, G, a.rows);

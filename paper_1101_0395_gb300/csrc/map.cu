@@ -5,8 +5,7 @@
 // into a 2^24-entry byte table at its key and adding w * d to the error sum; the
 // pixel stream (map_pixels) then reads 48 bytes per 16 pixels, looks each key up
 // in the table (16 MiB, resident in L2) and writes 16 indices with one 16-byte
-// store.  Distances between 8-bit colours are integers below 2^18, so FP32
-// arithmetic on them is exact and the argmin is the integer argmin.
+// store.  Distances between 8-bit colours are exact integers below 2^18.
 #include "kq_dev.cuh"
 
 namespace kq {
@@ -15,33 +14,43 @@ namespace {
 constexpr int kLutBlock = 256;
 constexpr int kPixBlock = 256;
 
+// Nearest palette entry of each unique colour.  With colours as byte vectors,
+// |x - p|^2 = |x|^2 + |p|^2 - 2 x.p is an exact integer below 2^18, the dot product
+// one dp4a; the value (d << 8) | k then orders by distance and, on ties, by the
+// lower index, so one 32-bit minimum per palette entry gives the exact argmin.
+// Each thread takes two colours per pass over the palette.
 __global__ void __launch_bounds__(kLutBlock) map_lut(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ w,
                                                      const int32_t *n_unique, const uint8_t *__restrict__ palette,
                                                      int K, uint8_t *__restrict__ lut,
                                                      unsigned long long *__restrict__ sse_num)
 {
-    __shared__ float4 s_p[kMaxK];
+    __shared__ uint2 s_p[kMaxK];  // .x packed colour, .y = (|p|^2 << 8) | k
     __shared__ unsigned long long s_red[kLutBlock / 32];
-    for (int k = threadIdx.x; k < K; k += kLutBlock)
-        s_p[k] = make_float4((float)palette[3 * k], (float)palette[3 * k + 1], (float)palette[3 * k + 2], 0.f);
+    for (int k = threadIdx.x; k < K; k += kLutBlock) {
+        const uint32_t r = palette[3 * k], g = palette[3 * k + 1], bb = palette[3 * k + 2];
+        s_p[k] = make_uint2((r << 16) | (g << 8) | bb, ((r * r + g * g + bb * bb) << 8) | (uint32_t)k);
+    }
     __syncthreads();
     const int64_t n = *n_unique;
     unsigned long long acc = 0ull;
-    for (int64_t i = (int64_t)blockIdx.x * kLutBlock + threadIdx.x; i < n; i += (int64_t)gridDim.x * kLutBlock) {
-        const uint32_t key = keys[i];
-        const float x = (float)key_r(key), y = (float)key_g(key), z = (float)key_b(key);
-        float best = __int_as_float(0x7f800000);
-        int arg = 0;
+    const int64_t stride = (int64_t)gridDim.x * kLutBlock * 2;
+    for (int64_t i0 = ((int64_t)blockIdx.x * kLutBlock + threadIdx.x) * 2; i0 < n; i0 += stride) {
+        const bool two = i0 + 1 < n;
+        const uint32_t ka = keys[i0], kb = two ? keys[i0 + 1] : ka;
+        const uint32_t ba = __dp4a(ka, ka, 0u) << 8, bbv = __dp4a(kb, kb, 0u) << 8;
+        uint32_t ma = 0xFFFFFFFFu, mb = 0xFFFFFFFFu;
+#pragma unroll 8
         for (int k = 0; k < K; ++k) {
-            const float4 p = s_p[k];
-            const float d = dist3(x, y, z, p.x, p.y, p.z);
-            if (d < best) {
-                best = d;
-                arg = k;
-            }
+            const uint2 pk = s_p[k];
+            ma = min(ma, ba + pk.y - (__dp4a(ka, pk.x, 0u) << 9));
+            mb = min(mb, bbv + pk.y - (__dp4a(kb, pk.x, 0u) << 9));
         }
-        lut[key] = (uint8_t)arg;
-        acc += (unsigned long long)w[i] * (unsigned long long)best;
+        lut[ka] = (uint8_t)(ma & 0xFFu);
+        acc += (unsigned long long)w[i0] * (ma >> 8);
+        if (two) {
+            lut[kb] = (uint8_t)(mb & 0xFFu);
+            acc += (unsigned long long)w[i0 + 1] * (mb >> 8);
+        }
     }
     if (sse_num) {
         const unsigned long long t = block_sum_u64<kLutBlock>(acc, s_red);

@@ -389,8 +389,8 @@ __global__ void __launch_bounds__(kFarBlock, 1) seed_far(FarArgs a)
 // by round, so a CTA that starts the next round never overwrites what another CTA
 // may still be reading.
 constexpr int kClBlock = 1024;
-constexpr int kClElems = 12;                       // colours per thread
-constexpr int kClPer = kClBlock * kClElems;        // colours per CTA (12288)
+constexpr int kClElems = 11;                       // colours per thread at most (odd: see kernel)
+constexpr int kClPer = kClBlock * kClElems;        // colours per CTA (11264)
 
 struct ClusterArgs {
     const uint32_t *keys;
@@ -464,10 +464,19 @@ __global__ void __launch_bounds__(kClBlock, 1) seed_far_cluster(ClusterArgs a)
     const int64_t per = (n + C - 1) / C;
     const int64_t lo = (int64_t)rank * per < n ? (int64_t)rank * per : n;
     const int cnt = (int)((lo + per < n ? lo + per : n) - lo);
-    const int ept = (cnt + kClBlock - 1) / kClBlock;  // colours per thread, thread t owns [t ept, t ept + ept)
+    // Thread t owns local colours [t ept, t ept + ept), stored at shared slots
+    // t eps + k with an odd stride eps >= ept, so a warp's accesses hit distinct banks.
+    const int ept = (cnt + kClBlock - 1) / kClBlock;
+    const int eps = ept | 1;
     for (int j = tid; j < kClPer; j += kClBlock) {
-        s_key[j] = j < cnt ? a.keys[lo + j] : 0u;
-        s_w[j] = j < cnt ? a.w[lo + j] : 0u;
+        s_key[j] = 0u;
+        s_w[j] = 0u;
+    }
+    __syncthreads();
+    for (int j = tid; j < cnt; j += kClBlock) {
+        const int slot = (j / ept) * eps + j % ept;
+        s_key[slot] = a.keys[lo + j];
+        s_w[slot] = a.w[lo + j];
     }
     __syncthreads();
     uint32_t ckey = 0u, cnorm = 0u;
@@ -479,8 +488,8 @@ __global__ void __launch_bounds__(kClBlock, 1) seed_far_cluster(ClusterArgs a)
         if (r > 0 || a.mode == 0) {
 #pragma unroll 4
             for (int k = 0; k < ept; ++k) {
-                const int j = tid * ept + k;
-                if (j < cnt) {
+                const int j = tid * eps + k;
+                if (tid * ept + k < cnt) {
                     if (r == 0) {
                         acc += s_w[j];  // k-means++ first centre: probability w / sum w
                     } else {
@@ -571,8 +580,8 @@ __global__ void __launch_bounds__(kClBlock, 1) seed_far_cluster(ClusterArgs a)
             unsigned long long pk = 0ull;
             uint32_t kk = 0u;
             if (lane < gept) {
-                const int j = ts * gept + lane;
-                if (j < gcnt) {
+                const int j = ts * (gept | 1) + lane;
+                if (ts * gept + lane < gcnt) {
                     kk = dsmem_ld32(dsmem_addr(&s_key[j], g));
                     const unsigned long long wj = dsmem_ld32(dsmem_addr(&s_w[j], g));
                     pk = r == 0 ? wj : wj * (unsigned long long)dsmem_ld32(dsmem_addr(&d2[j], g));

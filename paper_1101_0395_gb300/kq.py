@@ -178,7 +178,7 @@ def parse_stats(stats: torch.Tensor) -> dict:
 def launches(call: str, n_pixels: int = 1, scheme: str = "KPP", K: int = 1) -> int:
     """Kernels one call enqueues (the library's own kernels, not memsets)."""
     if call == "kq_histogram":
-        return 3 if n_pixels > 0 else 2
+        return 4 if n_pixels > 0 else 3
     if call == "kq_lloyd":
         return 1
     if call == "kq_map":
