@@ -180,6 +180,99 @@ KQ_API int kq_map(const uint8_t *rgb, int64_t n_pixels, const uint32_t *keys, co
            const int32_t *n_unique, const uint8_t *palette, int32_t K, uint8_t *idx, int64_t *sse_num, void *ws,
            size_t ws_bytes, kq_stream_t stream);
 
+/* ------------------------------------------------------------------ batches
+ * Many images of uneven size and K in one persistent launch (the paper treats
+ * one image at a time; this runs its four steps for every image of a batch).
+ * Each image is taken from start to finish -- histogram, seeding, Weighted
+ * Sort-Means, mapping -- by one group of thread blocks: a thread-block cluster of
+ * `cluster` CTAs for images of more than `split_pixels` pixels, one CTA for the
+ * others.  Groups pull images from a device-side queue in the order of
+ * kq_batch_plan (largest estimated work first).  Per image the results are those
+ * of kq_histogram, kq_seed, kq_lloyd and kq_map on the same inputs, except that
+ * the FP32 SSE partials are summed over a different partition of blocks (the
+ * stop test can therefore differ only when (SSE_{i-1} - SSE_i) / SSE_i lies within
+ * about 1e-6 relative of eps).
+ */
+
+/* Per-image results, written by kq_batch_run (device memory, caller-owned). */
+typedef struct kq_batch_result {
+    int32_t status;       /* KQ_OK, KQ_EINVAL (bad item) or KQ_ECAPACITY (N' > capacity) */
+    int32_t n_unique;     /* N' (also when above capacity) */
+    kq_lloyd_stats lloyd; /* the final Lloyd run, as kq_lloyd writes it */
+    int64_t sse_num;      /* sum over pixels of |pixel - palette[idx]|^2 (MSE numerator, Eq. 2) */
+} kq_batch_result;
+
+/* One image of a batch.  Host and device use the same layout: the array passed
+ * to kq_batch_run is a device copy of the host array given to kq_batch_plan.
+ * All pointers are device pointers owned by the caller. */
+typedef struct kq_batch_item {
+    const uint8_t *rgb;       /* n_pixels x 3 bytes, packed RGB8, any alignment */
+    uint8_t *idx;             /* out: n_pixels palette indices */
+    uint32_t *keys;           /* out: capacity entries, unique colours ascending */
+    uint32_t *weights;        /* out: capacity entries, pixel counts */
+    uint8_t *labels;          /* out: capacity entries, last assignment */
+    void *scratch;            /* kq_batch_scratch_bytes(capacity) bytes, 256-byte aligned */
+    double *centers;          /* K x 3; in for KQ_INIT_USER, out: final centres */
+    uint8_t *palette;         /* out: K x 3 bytes (rounding as kq_lloyd) */
+    kq_batch_result *result;  /* out */
+    int64_t n_pixels;         /* >= 0 */
+    uint64_t seed;            /* random stream seed of the scheme */
+    double eps;               /* stop test of kq_lloyd */
+    double lbg_eps;           /* KQ_INIT_LBG: split perturbation (kq_seed_params.lbg_eps) */
+    double lbg_conv_eps;      /* KQ_INIT_LBG: refinement threshold */
+    int32_t lbg_max_iter;     /* KQ_INIT_LBG: refinement pass limit (>= 1 for LBG) */
+    int32_t K;                /* 1..256 */
+    int32_t scheme;           /* kq_init */
+    int32_t max_iter;         /* >= 1 */
+    int32_t capacity;         /* length of keys / weights / labels; min(n_pixels, 2^24) always suffices */
+    int32_t reserved;         /* 0 */
+} kq_batch_item;
+
+/* Launch shape: cluster size (1, 2, 4, 8 or 16; 1 = single CTAs only) and the
+ * pixel count above which an image goes to a cluster. */
+typedef struct kq_batch_config {
+    int32_t cluster;
+    int32_t reserved;
+    int64_t split_pixels;
+} kq_batch_config;
+
+/* Bytes of kq_batch_item.scratch for `capacity` unique colours (D^2 and the
+ * k-means++ step sums). */
+KQ_API size_t kq_batch_scratch_bytes(int32_t capacity);
+
+/* Workspace bytes of kq_batch_run on the current device: one slot of about
+ * 69 MiB (counter table, bitmaps, seeding and Lloyd scratch) per resident CTA.
+ * Zero-fill it once before first use (the library keeps its tables zeroed). */
+KQ_API size_t kq_batch_workspace_size(void);
+
+/* Largest cluster size kq_batch_run can launch on the current device (>= 1). */
+KQ_API int32_t kq_batch_max_cluster(void);
+
+/* Host-side planner: validates h_items (KQ_EINVAL on a bad item) and writes the
+ * processing order to h_order (n_items entries): first the images above
+ * cfg->split_pixels (when cfg->cluster > 1), then the rest, each class in
+ * decreasing n_pixels * (1 + K / 12).  *h_n_big = size of the first class. */
+KQ_API int kq_batch_plan(const kq_batch_item *h_items, int32_t n_items, const kq_batch_config *cfg, int32_t *h_order,
+                         int32_t *h_n_big);
+
+/* Runs the whole batch: one memset of the queue counters and one launch,
+ * asynchronous on `stream` (capturable in a CUDA graph).  `order` is a device copy
+ * of kq_batch_plan's order, n_big its class split.  Per-image errors go to the
+ * item's result; argument errors return KQ_EINVAL, a workspace smaller than
+ * kq_batch_workspace_size() for this cluster size KQ_ENOMEM.  The workspace
+ * must not be shared with a concurrent call. */
+KQ_API int kq_batch_run(const kq_batch_item *items, int32_t n_items, const int32_t *order, int32_t n_big,
+                        const kq_batch_config *cfg, void *ws, size_t ws_bytes, kq_stream_t stream);
+
+/* Autotuner: times kq_batch_run on this batch for each launch shape the device
+ * supports (single CTAs; clusters of 2..16 with split_pixels 2^18, 2^20, 2^22),
+ * keeps the fastest (best of two timed runs after a warm-up), writes its order
+ * to `order` (device) and returns the shape, its n_big and its time (ms).
+ * Synchronizes `stream`; the items' outputs hold the last timed run. */
+KQ_API int kq_batch_tune(const kq_batch_item *h_items, const kq_batch_item *items, int32_t n_items, int32_t *order,
+                         kq_batch_config *h_best, int32_t *h_n_big, float *h_best_ms, void *ws, size_t ws_bytes,
+                         kq_stream_t stream);
+
 /*
  * kq_lloyd without a workspace (the paper has no counterpart: this entry point
  * exists for callers of this library that cannot allocate device memory -- for

@@ -1,0 +1,460 @@
+// lloyd_body.cuh -- the Weighted Sort-Means iteration (Algorithm 2) as a device
+// function over a group of blocks, shared by the whole-grid kernel (lloyd.cu) and
+// the batched kernel (batch.cu), which differ only in their barrier.
+#pragma once
+
+#include "kq_dev.cuh"
+
+namespace kq {
+namespace {
+
+constexpr int kLloydBlock = 512;
+constexpr int kPtsPerThread = 1;  // blocks used = ceil(N' / (block * this)), capped by the launch
+// Row padding entry: distance bits of a huge finite float, so the scan always stops on it.
+constexpr uint32_t kPadEntry = 0x7F7FFF00u;
+// The first kRowCache entries of every row are copied to shared memory each pass
+// (row stride kRowCache + 1 words, so lanes reading different rows hit different banks).
+constexpr int kRowCache = 32;
+constexpr int kRowStride = kRowCache + 1;
+constexpr float kPruneSlack = 1.0f + 0x1p-17f;
+constexpr unsigned kFull = 0xffffffffu;
+
+struct LloydArgs {
+    const uint32_t *keys;
+    const uint32_t *w;
+    const int32_t *n_unique;
+    int K;
+    double eps;
+    int max_iter;
+    uint32_t flags;
+    int skip_if_n_le;
+    double *centers;
+    uint8_t *labels;
+    uint8_t *palette;
+    kq_lloyd_stats *stats;
+    double *sse_hist;
+    Ctl *ctl;                  // grid barrier of the whole-grid launch (unused by groups)
+    unsigned long long *ndc;   // distance count of the call
+    const int32_t *status;     // device status word reported in the statistics
+    unsigned long long *sums;  // [3][kMaxK][4]: pass i adds into buffer i % 3
+    float *sse_part;           // [2][kMaxGrid] block SSE partials (FP32, fixed-order trees)
+    uint32_t *rows;            // [K][Kp], Kp = K rounded up to a multiple of 4
+    float4 *cent;              // [K] FP32 centres published by their owner blocks
+};
+
+struct LloydShared {
+    float4 c[kMaxK];
+    float cx[kMaxK], cy[kMaxK], cz[kMaxK];  // the same FP32 centres, one array per channel
+    double c64[kMaxK * 3];
+    unsigned long long sum[kMaxK * 4];
+    uint32_t sum32[kMaxK * 4];  // used instead of sum when the block's sums fit 32 bits
+    uint32_t row[2][kMaxK];
+    float red_f[kLloydBlock / 32];
+    unsigned long long red_u[kLloydBlock / 32];
+    double sse_i;
+    int conv;
+    int narrow;
+};
+
+// Rows p = b, b + G, b + 2G, ... of the sorted centre-distance table; the two
+// halves of the block build two rows at once.  Entry rank = number of smaller
+// packed entries (the index in the low byte makes every entry distinct).
+__device__ __forceinline__ void build_rows(LloydShared &sh, int K, int b, int G, uint32_t *rows)
+{
+    constexpr int kHalf = kLloydBlock / 2;  // >= kMaxK
+    const int Kp = (K + 3) & ~3;
+    const int hs = threadIdx.x / kHalf, ht = threadIdx.x % kHalf;
+    for (int m = 0; b + G * m < K; m += 2) {
+        const int p = b + G * (m + hs);
+        const bool act = p < K;
+        if (ht < Kp) {
+            uint32_t v = 0xFFFFFFFFu;
+            if (act && ht < K) {
+                const float4 cp = sh.c[p], ct = sh.c[ht];
+                const float d = dist3(cp.x, cp.y, cp.z, ct.x, ct.y, ct.z);
+                v = (__float_as_uint(d) & 0xFFFFFF00u) | (uint32_t)ht;
+            }
+            sh.row[hs][ht] = v;
+        }
+        __syncthreads();
+        if (act && ht < Kp) {
+            if (ht < K) {
+                const uint32_t v = sh.row[hs][ht];
+                const uint4 *r4 = reinterpret_cast<const uint4 *>(sh.row[hs]);
+                int r = 0;
+#pragma unroll 8
+                for (int u = 0; u < Kp / 4; ++u) {
+                    const uint4 q = r4[u];
+                    r += (q.x < v) + (q.y < v) + (q.z < v) + (q.w < v);
+                }
+                rows[(size_t)p * Kp + r] = v;
+            } else {
+                rows[(size_t)p * Kp + ht] = kPadEntry;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ void set_centre(LloydShared &sh, int k, float4 c)
+{
+    sh.c[k] = c;
+    sh.cx[k] = c.x;
+    sh.cy[k] = c.y;
+    sh.cz[k] = c.z;
+}
+
+// Full search over all K centres with the lowest index winning ties.  Distances are
+// taken eight at a time and folded with fminf; the running best moves only on a
+// strictly smaller group minimum (so the earliest group holding the minimum wins),
+// and the winning group is evaluated again to find its first centre at that
+// distance.  The same dist3 values as a one-at-a-time scan, so the same argmin.
+__device__ __forceinline__ void dense_argmin(const LloydShared &sh, int K, float x, float y, float z, float &best,
+                                             int &arg)
+{
+    best = __int_as_float(0x7f800000);
+    int bg = -1;
+    int k0 = 0;
+    for (; k0 + 8 <= K; k0 += 8) {
+        float d[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) d[j] = dist3(x, y, z, sh.cx[k0 + j], sh.cy[k0 + j], sh.cz[k0 + j]);
+        const float m = fminf(fminf(fminf(d[0], d[1]), fminf(d[2], d[3])), fminf(fminf(d[4], d[5]), fminf(d[6], d[7])));
+        if (m < best) {
+            best = m;
+            bg = k0;
+        }
+    }
+    arg = 0;
+    if (bg >= 0) {
+#pragma unroll
+        for (int j = 7; j >= 0; --j)
+            if (dist3(x, y, z, sh.cx[bg + j], sh.cy[bg + j], sh.cz[bg + j]) == best) arg = bg + j;
+    }
+    for (int k = k0; k < K; ++k) {
+        const float d = dist3(x, y, z, sh.cx[k], sh.cy[k], sh.cz[k]);
+        if (d < best) {
+            best = d;
+            arg = k;
+        }
+    }
+}
+
+// Adds (w R, w G, w B, w) of each lane's point to its cluster's block sums.  When
+// all lanes of the warp chose the same cluster, one lane adds the warp total.
+// `narrow`: the block's whole slice has sum(w) * 255 < 2^32, so 32-bit sums are
+// exact and the native 32-bit shared-memory atomics can be used.
+__device__ __forceinline__ void warp_accumulate(LloydShared &sh, bool narrow, bool active, int arg, uint32_t w,
+                                                uint32_t key)
+{
+    const int a0 = __shfl_sync(kFull, arg, 0);
+    const bool same = __all_sync(kFull, !active || arg == a0);
+    if (narrow) {
+        uint32_t W = active ? w : 0u;
+        uint32_t r = W * key_r(key), g = W * key_g(key), bb = W * key_b(key);
+        if (same) {
+            for (int o = 16; o; o >>= 1) {
+                r += __shfl_down_sync(kFull, r, o);
+                g += __shfl_down_sync(kFull, g, o);
+                bb += __shfl_down_sync(kFull, bb, o);
+                W += __shfl_down_sync(kFull, W, o);
+            }
+            if ((threadIdx.x & 31) == 0 && W) {
+                atomicAdd(&sh.sum32[a0 * 4 + 0], r);
+                atomicAdd(&sh.sum32[a0 * 4 + 1], g);
+                atomicAdd(&sh.sum32[a0 * 4 + 2], bb);
+                atomicAdd(&sh.sum32[a0 * 4 + 3], W);
+            }
+        } else if (active) {
+            atomicAdd(&sh.sum32[arg * 4 + 0], r);
+            atomicAdd(&sh.sum32[arg * 4 + 1], g);
+            atomicAdd(&sh.sum32[arg * 4 + 2], bb);
+            atomicAdd(&sh.sum32[arg * 4 + 3], W);
+        }
+        return;
+    }
+    unsigned long long W = active ? (unsigned long long)w : 0ull;
+    unsigned long long r = W * key_r(key), g = W * key_g(key), bb = W * key_b(key);
+    if (same) {
+        for (int o = 16; o; o >>= 1) {
+            r += __shfl_down_sync(kFull, r, o);
+            g += __shfl_down_sync(kFull, g, o);
+            bb += __shfl_down_sync(kFull, bb, o);
+            W += __shfl_down_sync(kFull, W, o);
+        }
+        if ((threadIdx.x & 31) == 0 && W) {
+            atomicAdd(&sh.sum[a0 * 4 + 0], r);
+            atomicAdd(&sh.sum[a0 * 4 + 1], g);
+            atomicAdd(&sh.sum[a0 * 4 + 2], bb);
+            atomicAdd(&sh.sum[a0 * 4 + 3], W);
+        }
+    } else if (active) {
+        atomicAdd(&sh.sum[arg * 4 + 0], r);
+        atomicAdd(&sh.sum[arg * 4 + 1], g);
+        atomicAdd(&sh.sum[arg * 4 + 2], bb);
+        atomicAdd(&sh.sum[arg * 4 + 3], W);
+    }
+}
+
+// The Lloyd iteration run by G blocks (ranks b = 0..G-1) over n unique colours.
+// `sync` is a barrier across the G blocks that orders their global memory
+// accesses; it returns false when the wait gave up, and the blocks then return.
+template <class Sync>
+__device__ __forceinline__ void lloyd_body(const LloydArgs &a, LloydShared &sh, uint32_t *row_cache, int64_t n, int b,
+                                           int G, Sync &sync)
+{
+    const int K = a.K;
+    const int Kp = (K + 3) & ~3;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int kWarps = kLloydBlock / 32;
+    const bool prune = !(a.flags & KQ_LLOYD_DENSE);
+    const bool labels_in = (a.flags & KQ_LLOYD_LABELS_IN) != 0;
+    const int64_t nch = (n + 31) / 32;  // 32-colour chunks; this block takes b, b + G, ...
+
+    for (int k = tid; k < K; k += kLloydBlock) {
+        const double x = a.centers[3 * k], y = a.centers[3 * k + 1], z = a.centers[3 * k + 2];
+        sh.c64[3 * k] = x;
+        sh.c64[3 * k + 1] = y;
+        sh.c64[3 * k + 2] = z;
+        set_centre(sh, k, make_float4((float)x, (float)y, (float)z, 0.f));
+    }
+    {
+        unsigned long long sw = 0ull;
+        for (int64_t c = b + (int64_t)G * warp; c < nch; c += (int64_t)G * kWarps) {
+            const int64_t i = c * 32 + lane;
+            if (i < n) sw += a.w[i];
+        }
+        sw = block_sum_u64<kLloydBlock>(sw, sh.red_u);
+        if (tid == 0) sh.narrow = sw * 255ull < (1ull << 32) ? 1 : 0;
+        __syncthreads();
+    }
+    const bool narrow = sh.narrow != 0;
+    if (prune) build_rows(sh, K, b, G, a.rows);
+    if (b == 0) {
+        for (int j = tid; j < 3 * kMaxK * 4; j += kLloydBlock) a.sums[j] = 0ull;
+        if (tid == 0) *a.ndc = 0ull;
+    }
+    if (!sync()) return;
+
+    double prev_sse = 0.0;
+    int it = 0;
+    for (;;) {
+        // ---- A: assignment
+        const int buf = it & 1;
+        unsigned long long *gsum = a.sums + (size_t)(it % 3) * kMaxK * 4;
+        for (int j = tid; j < K * 4; j += kLloydBlock) {
+            sh.sum[j] = 0ull;
+            sh.sum32[j] = 0u;
+        }
+        const bool use_prev = prune && (labels_in || it > 0);
+        if (use_prev) {
+            // the first kRowCache entries of every row, 16 bytes per load
+            constexpr int kQ = kRowCache / 4;
+            for (int j = tid; j < K * kQ; j += kLloydBlock) {
+                const int pr = j / kQ, q4 = j % kQ;
+                uint4 v = make_uint4(kPadEntry, kPadEntry, kPadEntry, kPadEntry);
+                if (4 * q4 < Kp) v = __ldcg(reinterpret_cast<const uint4 *>(a.rows + (size_t)pr * Kp) + q4);
+                uint32_t *dst = row_cache + pr * kRowStride + 4 * q4;
+                dst[0] = v.x;
+                dst[1] = v.y;
+                dst[2] = v.z;
+                dst[3] = v.w;
+            }
+        }
+        __syncthreads();
+        float sse32 = 0.f;
+        unsigned long long ndc = 0ull;
+        for (int64_t c = b + (int64_t)G * warp; c < nch; c += (int64_t)G * kWarps) {
+            const int64_t i = c * 32 + lane;
+            const bool active = i < n;
+            uint32_t key = 0u, w = 0u;
+            int arg = 0;
+            float best = 0.f;
+            if (active) {
+                key = a.keys[i];
+                w = a.w[i];
+            }
+            if (use_prev) {
+                // Sort-means scan from the previous centre p.  Each lane first walks its own
+                // point's row through the shared-memory copy of the first kRowCache entries;
+                // points whose bound has not stopped them by then continue together, the
+                // whole warp testing 32 further entries of that point's row per step.
+                int p = active ? a.labels[i] : 0;
+                if (p >= K) p = 0;
+                const float x = (float)key_r(key), y = (float)key_g(key), z = (float)key_b(key);
+                const float4 cp = sh.c[p];
+                const float prev = dist3(x, y, z, cp.x, cp.y, cp.z);
+                const float thr = __fmul_rn(4.0f * prev, kPruneSlack);
+                float bd = prev;
+                uint32_t bt = (uint32_t)p;
+                bool done = !active;
+                const uint32_t *rc = row_cache + p * kRowStride;
+                const int jl = Kp < kRowCache ? Kp : kRowCache;
+                for (int j = 0; j < jl; ++j) {
+                    if (!done) {
+                        const uint32_t e = rc[j];
+                        if (__uint_as_float(e & 0xFFFFFF00u) > thr) {
+                            done = true;
+                        } else {
+                            const uint32_t t = e & 0xFFu;
+                            if (t != (uint32_t)p) {
+                                const float4 ct = sh.c[t];
+                                const float d = dist3(x, y, z, ct.x, ct.y, ct.z);
+                                ++ndc;
+                                if (d < bd || (d == bd && t < bt)) {
+                                    bd = d;
+                                    bt = t;
+                                }
+                            }
+                        }
+                    }
+                    if ((j & 7) == 7 && !__any_sync(kFull, !done)) break;
+                }
+                unsigned tail = __ballot_sync(kFull, !done && Kp > kRowCache);
+                while (tail) {
+                    const int q = __ffs(tail) - 1;
+                    tail &= tail - 1;
+                    const uint32_t kq = __shfl_sync(kFull, key, q);
+                    const int pq = __shfl_sync(kFull, p, q);
+                    const float thq = __shfl_sync(kFull, thr, q);
+                    float qd = __shfl_sync(kFull, bd, q);
+                    uint32_t qt = __shfl_sync(kFull, bt, q);
+                    const float qx = (float)key_r(kq), qy = (float)key_g(kq), qz = (float)key_b(kq);
+                    const uint32_t *row = a.rows + (size_t)pq * Kp;
+                    for (int j0 = kRowCache; j0 < Kp; j0 += 32) {
+                        const uint32_t e = (j0 + lane < Kp) ? __ldcg(row + j0 + lane) : kPadEntry;
+                        const bool brk = __uint_as_float(e & 0xFFFFFF00u) > thq;
+                        const unsigned bal = __ballot_sync(kFull, brk);
+                        const uint32_t t = e & 0xFFu;
+                        if (!brk && t != (uint32_t)pq) {
+                            const float4 ct = sh.c[t];
+                            const float d = dist3(qx, qy, qz, ct.x, ct.y, ct.z);
+                            ++ndc;
+                            if (d < qd || (d == qd && t < qt)) {
+                                qd = d;
+                                qt = t;
+                            }
+                        }
+                        if (bal) break;
+                    }
+                    const uint32_t md = __reduce_min_sync(kFull, __float_as_uint(qd));
+                    const uint32_t mt = __reduce_min_sync(kFull, __float_as_uint(qd) == md ? qt : 0xFFFFFFFFu);
+                    if (lane == q) {
+                        bd = __uint_as_float(md);
+                        bt = mt;
+                    }
+                }
+                if (active) {
+                    ++ndc;  // the distance to the previous centre
+                    best = bd;
+                    arg = (int)bt;
+                }
+            } else if (active) {
+                dense_argmin(sh, K, (float)key_r(key), (float)key_g(key), (float)key_b(key), best, arg);
+                ndc += (unsigned long long)K;
+            }
+            if (active) {
+                a.labels[i] = (uint8_t)arg;
+                // w < 2^32 and best are FP32; one rounding per product, FP64 above the thread
+                sse32 = __fadd_rn(sse32, __fmul_rn((float)w, best));
+            }
+            warp_accumulate(sh, narrow, active, arg, w, key);
+        }
+        const float bsse = block_sum_f32<kLloydBlock>(sse32, sh.red_f);
+        const unsigned long long bndc = block_sum_u64<kLloydBlock>(ndc, sh.red_u);
+        __syncthreads();
+        for (int j = tid; j < K * 4; j += kLloydBlock) {
+            const unsigned long long v = narrow ? (unsigned long long)sh.sum32[j] : sh.sum[j];
+            if (v) atomicAdd(gsum + j, v);
+        }
+        if (tid == 0) {
+            a.sse_part[(size_t)buf * kMaxGrid + b] = bsse;
+            atomicAdd(a.ndc, bndc);
+        }
+        if (!sync()) return;
+
+        // ---- B: SSE, stopping test, owned centres.  FP64 instructions are slow on
+        // this GPU, so the stopping test (warp 0) and the three channel divisions of
+        // the owned clusters (warps 1-3) run in different warps.
+        ++it;
+        if (warp == 0) {
+            float s = 0.f;
+            for (int g = lane; g < G; g += 32) s = __fadd_rn(s, __ldcg(a.sse_part + (size_t)buf * kMaxGrid + g));
+            for (int o = 16; o; o >>= 1) s = __fadd_rn(s, __shfl_down_sync(kFull, s, o));
+            if (lane == 0) {
+                const double si = (double)s;
+                bool conv = false;
+                if (a.eps >= 0.0) {
+                    if (si == 0.0) conv = true;
+                    else if (it > 1 && (prev_sse - si) / si <= a.eps) conv = true;
+                }
+                sh.sse_i = si;
+                sh.conv = conv ? 1 : 0;
+            }
+        } else if (warp <= 3) {
+            const int ch = warp - 1;
+            for (int k = b + G * lane; k < K; k += G * 32) {
+                const unsigned long long W = __ldcg(gsum + 4 * k + 3);
+                if (W) sh.c64[3 * k + ch] = (double)__ldcg(gsum + 4 * k + ch) / (double)W;
+            }
+        }
+        __syncthreads();
+        const double sse_i = sh.sse_i;
+        const bool conv = sh.conv != 0;
+        const bool stop = conv || it >= a.max_iter;
+        for (int k = b + G * tid; k < K; k += G * kLloydBlock) {
+            const unsigned long long W = __ldcg(gsum + 4 * k + 3);
+            const double x = sh.c64[3 * k], y = sh.c64[3 * k + 1], z = sh.c64[3 * k + 2];
+            a.cent[k] = make_float4((float)x, (float)y, (float)z, 0.f);
+            if (stop) {
+                a.centers[3 * k] = x;
+                a.centers[3 * k + 1] = y;
+                a.centers[3 * k + 2] = z;
+                for (int ch = 0; ch < 3; ++ch) {
+                    int v;
+                    if (W) {
+                        const unsigned long long S = __ldcg(gsum + 4 * k + ch);
+                        v = (int)((2ull * S + W) / (2ull * W));
+                    } else {
+                        const double f = floor(sh.c64[3 * k + ch] + 0.5);
+                        v = f < 0.0 ? 0 : (f > 255.0 ? 255 : (int)f);
+                    }
+                    a.palette[3 * k + ch] = (uint8_t)v;
+                }
+            }
+        }
+        if (b == 0) {
+            // Buffer (pass + 1) % 3 was last read in the previous pass and is next added
+            // into two passes from now, after barriers this block must reach first.
+            unsigned long long *ahead = a.sums + (size_t)((it + 1) % 3) * kMaxK * 4;
+            for (int j = tid; j < kMaxK * 4; j += kLloydBlock) ahead[j] = 0ull;
+            if (tid == 0 && a.sse_hist) a.sse_hist[it - 1] = sse_i;
+            if (stop && tid == 0 && a.stats) {
+                kq_lloyd_stats st;
+                st.iters = it;
+                st.converged = conv ? 1 : 0;
+                st.k_eff = (int32_t)(n < K ? n : K);
+                st.status = *(volatile const int32_t *)a.status;
+                st.ndc = (int64_t)*(volatile unsigned long long *)a.ndc;
+                st.sse = sse_i;
+                st.sse_prev = it > 1 ? prev_sse : 0.0;
+                *a.stats = st;
+            }
+        }
+        if (stop) return;
+        prev_sse = sse_i;
+        if (!sync()) return;
+
+        // ---- C: all centres, then this block's rows of the distance table
+        for (int k = tid; k < K; k += kLloydBlock) set_centre(sh, k, __ldcg(a.cent + k));
+        __syncthreads();
+        if (prune) {
+            build_rows(sh, K, b, G, a.rows);
+            if (!sync()) return;
+        }
+    }
+}
+
+
+}  // namespace
+}  // namespace kq

@@ -20,23 +20,14 @@
 //   LBG  centroid, then split rounds that call the Lloyd kernel.
 #include <math.h>
 
-#include "kq_dev.cuh"
+#include "seed_dev.cuh"
 
 namespace kq {
 namespace {
 
 constexpr int kFarBlock = 512;
 constexpr int kChunkBlock = 256;
-constexpr int kMapSlots = 8192;   // Fisher-Yates displacement map (positions + values)
-constexpr int kSffMax = 4096;     // ceil(2 * 256 * ln 256) = 2840 fits
 constexpr unsigned kFull = 0xffffffffu;
-
-__device__ __forceinline__ void key_to_centre(double *c, uint32_t key)
-{
-    c[0] = (double)key_r(key);
-    c[1] = (double)key_g(key);
-    c[2] = (double)key_b(key);
-}
 
 // ---------------------------------------------------------------- K >= N'
 // The centres are the N' unique colours in key order, padded with the last.
@@ -51,49 +42,6 @@ __global__ void seed_all_unique(const uint32_t *keys, const int32_t *n_unique, i
             key_to_centre(centers + 3 * k, keys[k < n ? k : n - 1]);
         }
     }
-}
-
-// ---------------------------------------------------------------- Fisher-Yates
-struct FyMap {
-    uint32_t *pos1;  // position + 1, 0 = empty
-    uint32_t *val;
-    uint32_t mask;
-};
-
-__device__ __forceinline__ uint32_t fy_slot(uint32_t pos, uint32_t mask) { return (pos * 2654435761u) & mask; }
-
-__device__ uint32_t fy_get(const FyMap &m, uint32_t pos)
-{
-    for (uint32_t h = fy_slot(pos, m.mask);; h = (h + 1) & m.mask) {
-        if (m.pos1[h] == 0u) return pos;
-        if (m.pos1[h] == pos + 1u) return m.val[h];
-    }
-}
-
-__device__ void fy_set(const FyMap &m, uint32_t pos, uint32_t v)
-{
-    uint32_t h = fy_slot(pos, m.mask);
-    while (m.pos1[h] != 0u && m.pos1[h] != pos + 1u) h = (h + 1) & m.mask;
-    m.pos1[h] = pos + 1u;
-    m.val[h] = v;
-}
-
-// The first `count` entries of a uniformly random permutation of 0..n-1
-// (single thread; the map must hold 2 * count entries).
-__device__ void fisher_yates(uint32_t n, uint32_t count, uint64_t seed, uint32_t stream, const FyMap &m, uint32_t *out)
-{
-    for (uint32_t j = 0; j < count; ++j) {
-        const uint32_t r = j + (uint32_t)below(rand64(seed, stream, j), (uint64_t)(n - j));
-        const uint32_t vj = fy_get(m, j), vr = fy_get(m, r);
-        fy_set(m, j, vr);
-        fy_set(m, r, vj);
-        out[j] = vr;
-    }
-}
-
-__device__ void clear_map(uint32_t *pos1, int slots)
-{
-    for (int i = threadIdx.x; i < slots; i += blockDim.x) pos1[i] = 0u;
 }
 
 // Forgy: K distinct unique colours drawn uniformly (Algorithm 2, first line).
@@ -120,66 +68,9 @@ __global__ void __launch_bounds__(kSffBlock) seed_sff(const uint32_t *keys, cons
                                                       uint64_t seed, int s0, double *centers)
 {
     extern __shared__ uint32_t smem[];
-    __shared__ unsigned long long s_red[kSffBlock / 32];
-    __shared__ uint32_t s_cur;
     const int64_t n = *n_unique;
     if (n <= K) return;
-    const uint32_t s = (uint32_t)(s0 < n ? s0 : n);
-    FyMap m{smem, smem + kMapSlots, kMapSlots - 1};
-    uint32_t *sub = smem + 2 * kMapSlots;   // kSffMax entries
-    uint32_t *mind = sub + kSffMax;         // kSffMax entries
-    clear_map(m.pos1, kMapSlots);
-    __syncthreads();
-    if (threadIdx.x == 0) fisher_yates((uint32_t)n, s, seed, 4, m, sub);
-    __syncthreads();
-    for (uint32_t i = s + threadIdx.x; i < kSffMax; i += kSffBlock) sub[i] = 0xFFFFFFFFu;
-    __syncthreads();
-    // bitonic sort of kSffMax entries, ascending
-    for (int size = 2; size <= kSffMax; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int i = threadIdx.x; i < kSffMax; i += kSffBlock) {
-                const int j = i ^ stride;
-                if (j > i) {
-                    const bool up = (i & size) == 0;
-                    const uint32_t a = sub[i], b = sub[j];
-                    if ((a > b) == up) {
-                        sub[i] = b;
-                        sub[j] = a;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    }
-    if (threadIdx.x == 0) s_cur = (uint32_t)below(rand64(seed, 5, 0), (uint64_t)s);
-    __syncthreads();
-    uint32_t cur = s_cur;
-    if (threadIdx.x == 0) key_to_centre(centers, keys[sub[cur]]);
-    for (int k = 1; k < K; ++k) {
-        const uint32_t ck = keys[sub[cur]];
-        unsigned long long best = 0ull;
-        for (uint32_t i = threadIdx.x; i < s; i += kSffBlock) {
-            const uint32_t d = key_dist2(keys[sub[i]], ck);
-            const uint32_t md = (k == 1) ? d : min(mind[i], d);
-            mind[i] = md;
-            const unsigned long long packed = ((unsigned long long)md << 32) | (0xFFFFFFFFu - i);
-            best = packed > best ? packed : best;
-        }
-        for (int o = 16; o; o >>= 1) {
-            const unsigned long long other = __shfl_down_sync(kFull, best, o);
-            best = other > best ? other : best;
-        }
-        if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = best;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            unsigned long long b = 0ull;
-            for (int wv = 0; wv < kSffBlock / 32; ++wv) b = s_red[wv] > b ? s_red[wv] : b;
-            s_cur = 0xFFFFFFFFu - (uint32_t)(b & 0xFFFFFFFFull);
-            key_to_centre(centers + 3 * k, keys[sub[s_cur]]);
-        }
-        __syncthreads();
-        cur = s_cur;
-    }
+    sff_block(keys, n, K, seed, s0, centers, smem);
 }
 
 // ---------------------------------------------------------------- KPP / MMX
@@ -210,13 +101,6 @@ struct FarShared {
 
 constexpr int kFarPer = 4;                    // consecutive colours per thread and chunk
 constexpr int kFarChunk = kFarBlock * kFarPer;
-
-// Minmax candidate: larger D^2 first, then the lower key (keys ascend with the
-// index, so this is the lowest index among ties).
-__device__ __forceinline__ unsigned long long mmx_pack(uint32_t d2, uint32_t key)
-{
-    return ((unsigned long long)d2 << 24) | (unsigned long long)(0xFFFFFFu - key);
-}
 
 // k-means++ sampling by inverse CDF.  With total = sum of the G block partials
 // and t = below(u, total), the sample is the first colour whose running sum of
@@ -606,11 +490,6 @@ __global__ void __launch_bounds__(kClBlock, 1) seed_far_cluster(ClusterArgs a)
 }
 
 // ---------------------------------------------------------------- chunked counts (VAR, DEN)
-__device__ __forceinline__ int den_cell(uint32_t key)
-{
-    return (int)(((key >> 22) & 3u) * 16u + ((key >> 14) & 3u) * 4u + ((key >> 6) & 3u));
-}
-
 __device__ __forceinline__ int64_t chunk_len(int64_t n) { return (n + kSeedChunks - 1) / kSeedChunks; }
 
 // mode 0 (VAR): per chunk, counts of each value of each channel; exact moments.
@@ -669,53 +548,6 @@ __global__ void __launch_bounds__(kChunkBlock) seed_chunk_counts(const uint32_t 
     }
 }
 
-// Warp-level: index of the element of rank `j` (0-based, in key order) among the
-// unique colours whose class (channel value or cell) equals `cls`.
-__device__ int64_t warp_locate(const uint32_t *keys, int64_t n, const uint32_t *chunk_cnt, int width, int col,
-                               uint32_t j, int mode, int ch)
-{
-    const int lane = threadIdx.x & 31;
-    const int64_t len = chunk_len(n);
-    // chunk holding the element
-    uint32_t run = 0;
-    int cstar = kSeedChunks - 1;
-    for (int base = 0; base < kSeedChunks; base += 32) {
-        const uint32_t v = chunk_cnt[(size_t)(base + lane) * width + col];
-        uint32_t x = v;
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(kFull, x, o);
-            if (lane >= o) x += y;
-        }
-        const unsigned bal = __ballot_sync(kFull, run + x > j);
-        if (bal) {
-            const int l = __ffs(bal) - 1;
-            cstar = base + l;
-            run += __shfl_sync(kFull, x, l) - __shfl_sync(kFull, v, l);
-            break;
-        }
-        run += __shfl_sync(kFull, x, 31);
-    }
-    uint32_t r = j - run;
-    const int64_t lo = (int64_t)cstar * len, hi = lo + len < n ? lo + len : n;
-    for (int64_t base = lo; base < hi; base += 32) {
-        const int64_t i = base + lane;
-        bool match = false;
-        if (i < hi) {
-            const uint32_t key = keys[i];
-            match = mode == 0 ? (int)((key >> (16 - 8 * ch)) & 255u) == col - ch * 256 : den_cell(key) == col;
-        }
-        const unsigned bal = __ballot_sync(kFull, match);
-        const uint32_t c = __popc(bal);
-        if (r < c) {
-            unsigned m = bal;
-            for (uint32_t q = 0; q < r; ++q) m &= m - 1;
-            return base + (__ffs(m) - 1);
-        }
-        r -= c;
-    }
-    return hi > 0 ? hi - 1 : 0;  // unreachable with consistent counts
-}
-
 // ---------------------------------------------------------------- VAR
 __global__ void seed_var_pick(const uint32_t *keys, const int32_t *n_unique, int K, const uint32_t *chunk_cnt,
                               const uint32_t *gcnt, const Ctl *ctl, double *centers)
@@ -723,44 +555,9 @@ __global__ void seed_var_pick(const uint32_t *keys, const int32_t *n_unique, int
     const int64_t n = *n_unique;
     if (n <= K) return;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
     if (warp >= K) return;
-    // channel of largest weighted variance, compared as W * S2 - S1^2 (exact)
-    const unsigned __int128 W = ctl->var_w;
-    int ch = 0;
-    unsigned __int128 best = 0;
-    for (int c = 0; c < 3; ++c) {
-        const unsigned __int128 s1 = ctl->var_s1[c], s2 = ctl->var_s2[c];
-        const unsigned __int128 v = W * s2 - s1 * s1;
-        if (c == 0 || v > best) {
-            best = v;
-            ch = c;
-        }
-    }
-    const int g = warp;
-    const int64_t glo = (int64_t)g * n / K, ghi = (int64_t)(g + 1) * n / K;
-    const uint32_t m = (uint32_t)((glo + ghi - 1) / 2);
-    // value v holding rank m
-    uint32_t run = 0;
-    int v = 255;
-    for (int base = 0; base < 256; base += 32) {
-        const uint32_t cv = gcnt[ch * 256 + base + lane];
-        uint32_t x = cv;
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(kFull, x, o);
-            if (lane >= o) x += y;
-        }
-        const unsigned bal = __ballot_sync(kFull, run + x > m);
-        if (bal) {
-            const int l = __ffs(bal) - 1;
-            v = base + l;
-            run += __shfl_sync(kFull, x, l) - __shfl_sync(kFull, cv, l);
-            break;
-        }
-        run += __shfl_sync(kFull, x, 31);
-    }
-    const int64_t idx = warp_locate(keys, n, chunk_cnt, 3 * 256, ch * 256 + v, m - run, 0, ch);
-    if (lane == 0) key_to_centre(centers + 3 * g, keys[idx]);
+    const int ch = var_channel(ctl->var_w, ctl->var_s1, ctl->var_s2);
+    var_pick_warp(keys, n, K, warp, ch, chunk_cnt, kSeedChunks, gcnt, centers);
 }
 
 // ---------------------------------------------------------------- DEN
@@ -772,54 +569,7 @@ __global__ void seed_den_quota(const int32_t *n_unique, int K, const uint32_t *c
 {
     const int64_t n = *n_unique;
     if (n <= K || threadIdx.x != 0) return;
-    int64_t celln[kDenCells], q[kDenCells], rem[kDenCells];
-    int fixed[kDenCells];
-    for (int c = 0; c < kDenCells; ++c) {
-        celln[c] = celln_in[c];
-        fixed[c] = 0;
-    }
-    for (;;) {
-        int64_t seats = K;
-        unsigned long long wa = 0;
-        for (int c = 0; c < kDenCells; ++c) {
-            if (fixed[c]) seats -= celln[c];
-            else if (celln[c] > 0) wa += cellw[c];
-        }
-        int64_t given = 0;
-        for (int c = 0; c < kDenCells; ++c) {
-            q[c] = 0;
-            rem[c] = -1;
-            if (fixed[c]) {
-                q[c] = celln[c];
-            } else if (celln[c] > 0 && wa > 0) {
-                const unsigned long long num = (unsigned long long)seats * cellw[c];
-                q[c] = (int64_t)(num / wa);
-                rem[c] = (int64_t)(num % wa);
-                given += q[c];
-            }
-        }
-        for (int64_t left = seats - given; left > 0; --left) {
-            int arg = -1;
-            for (int c = 0; c < kDenCells; ++c)
-                if (rem[c] >= 0 && (arg < 0 || rem[c] > rem[arg])) arg = c;
-            q[arg] += 1;
-            rem[arg] = -1;
-        }
-        int grew = 0;
-        for (int c = 0; c < kDenCells; ++c) {
-            if (!fixed[c] && q[c] > celln[c]) {
-                fixed[c] = 1;
-                grew = 1;
-            }
-        }
-        if (!grew) break;
-    }
-    int off = 0;
-    for (int c = 0; c < kDenCells; ++c) {
-        quota_out[c] = (int)q[c];
-        quota_out[kDenCells + c] = off;
-        off += (int)q[c];
-    }
+    den_quota(K, celln_in, cellw, quota_out);
 }
 
 // One block per cell: a uniform draw without replacement among the cell's
@@ -841,7 +591,7 @@ __global__ void seed_den_pick(const uint32_t *keys, const int32_t *n_unique, int
     __syncthreads();
     const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int j = warp; j < q; j += nw) {
-        const int64_t idx = warp_locate(keys, n, chunk_cnt, kDenCells, cell, s_pick[j], 1, 0);
+        const int64_t idx = warp_locate(keys, n, chunk_cnt, kSeedChunks, kDenCells, cell, s_pick[j], 1, 0);
         if ((threadIdx.x & 31) == 0) key_to_centre(centers + 3 * (off + j), keys[idx]);
     }
 }
@@ -874,15 +624,6 @@ __global__ void seed_lbg_cluster_sums(const uint32_t *keys, const uint32_t *w, c
     }
 }
 
-// Exact per-cluster SSE about the mean is num / W with num = W Q - |S|^2.
-__device__ __forceinline__ bool sse_greater(unsigned __int128 na, unsigned long long wa, unsigned __int128 nb,
-                                            unsigned long long wb)
-{
-    if (wa == 0) return false;
-    if (wb == 0) return true;
-    return na * (unsigned __int128)wb > nb * (unsigned __int128)wa;
-}
-
 // Split round: c_j - eps stays at j, c_j + eps goes to m + q (q-th chosen, in
 // ascending j).  All clusters split when 2m <= K; otherwise the K - m clusters
 // of largest SSE (ties to the lower index).
@@ -891,39 +632,7 @@ __global__ void seed_lbg_split(const int32_t *n_unique, int K, int m, double eps
 {
     const int64_t n = *n_unique;
     if (n <= K || threadIdx.x != 0) return;
-    const int split = (2 * m <= K) ? m : K - m;
-    bool chosen[kMaxK];
-    for (int j = 0; j < m; ++j) chosen[j] = split == m;
-    if (split < m) {
-        for (int t = 0; t < split; ++t) {
-            int arg = -1;
-            unsigned __int128 na = 0;
-            unsigned long long wa = 0;
-            for (int k = 0; k < m; ++k) {
-                if (chosen[k]) continue;
-                const unsigned long long W = cs[5 * k + 3];
-                unsigned __int128 s2 = 0;
-                for (int ch = 0; ch < 3; ++ch) s2 += (unsigned __int128)cs[5 * k + ch] * cs[5 * k + ch];
-                const unsigned __int128 num = (unsigned __int128)W * cs[5 * k + 4] - s2;
-                if (arg < 0 || sse_greater(num, W, na, wa)) {
-                    arg = k;
-                    na = num;
-                    wa = W;
-                }
-            }
-            chosen[arg] = true;
-        }
-    }
-    int q = 0;
-    for (int j = 0; j < m; ++j) {
-        if (!chosen[j]) continue;
-        for (int ch = 0; ch < 3; ++ch) {
-            const double base = centers[3 * j + ch];
-            centers[3 * (m + q) + ch] = base + eps;
-            centers[3 * j + ch] = base - eps;
-        }
-        ++q;
-    }
+    lbg_split(K, m, eps, cs, centers);
 }
 
 constexpr size_t kClSmem = sizeof(uint32_t) * 4 * (size_t)kClPer;  // keys, weights, 2 x D^2

@@ -1,0 +1,343 @@
+// seed_dev.cuh -- pieces of the seeding schemes (Section 2.3) used both by the
+// single-image kernels (seed.cu) and by the batched kernel (batch.cu).
+#pragma once
+
+#include "kq_dev.cuh"
+
+namespace kq {
+namespace {
+
+constexpr int kMapSlots = 8192;  // Fisher-Yates displacement map (positions + values)
+constexpr int kSffMax = 4096;    // ceil(2 * 256 * ln 256) = 2840 fits
+constexpr unsigned kSeedFull = 0xffffffffu;
+
+__device__ __forceinline__ void key_to_centre(double *c, uint32_t key)
+{
+    c[0] = (double)key_r(key);
+    c[1] = (double)key_g(key);
+    c[2] = (double)key_b(key);
+}
+
+// ---------------------------------------------------------------- Fisher-Yates
+struct FyMap {
+    uint32_t *pos1;  // position + 1, 0 = empty
+    uint32_t *val;
+    uint32_t mask;
+};
+
+__device__ __forceinline__ uint32_t fy_slot(uint32_t pos, uint32_t mask) { return (pos * 2654435761u) & mask; }
+
+__device__ uint32_t fy_get(const FyMap &m, uint32_t pos)
+{
+    for (uint32_t h = fy_slot(pos, m.mask);; h = (h + 1) & m.mask) {
+        if (m.pos1[h] == 0u) return pos;
+        if (m.pos1[h] == pos + 1u) return m.val[h];
+    }
+}
+
+__device__ void fy_set(const FyMap &m, uint32_t pos, uint32_t v)
+{
+    uint32_t h = fy_slot(pos, m.mask);
+    while (m.pos1[h] != 0u && m.pos1[h] != pos + 1u) h = (h + 1) & m.mask;
+    m.pos1[h] = pos + 1u;
+    m.val[h] = v;
+}
+
+// The first `count` entries of a uniformly random permutation of 0..n-1
+// (single thread; the map must hold 2 * count entries).
+__device__ void fisher_yates(uint32_t n, uint32_t count, uint64_t seed, uint32_t stream, const FyMap &m, uint32_t *out)
+{
+    for (uint32_t j = 0; j < count; ++j) {
+        const uint32_t r = j + (uint32_t)below(rand64(seed, stream, j), (uint64_t)(n - j));
+        const uint32_t vj = fy_get(m, j), vr = fy_get(m, r);
+        fy_set(m, j, vr);
+        fy_set(m, r, vj);
+        out[j] = vr;
+    }
+}
+
+__device__ void clear_map(uint32_t *pos1, int slots)
+{
+    for (int i = threadIdx.x; i < slots; i += blockDim.x) pos1[i] = 0u;
+}
+
+// Minmax candidate: larger D^2 first, then the lower key (keys ascend with the
+// index, so this is the lowest index among ties).
+__device__ __forceinline__ unsigned long long mmx_pack(uint32_t d2, uint32_t key)
+{
+    return ((unsigned long long)d2 << 24) | (unsigned long long)(0xFFFFFFu - key);
+}
+
+__device__ __forceinline__ int den_cell(uint32_t key)
+{
+    return (int)(((key >> 22) & 3u) * 16u + ((key >> 14) & 3u) * 4u + ((key >> 6) & 3u));
+}
+
+
+// Exact per-cluster SSE about the mean is num / W with num = W Q - |S|^2.
+__device__ __forceinline__ bool sse_greater(unsigned __int128 na, unsigned long long wa, unsigned __int128 nb,
+                                            unsigned long long wb)
+{
+    if (wa == 0) return false;
+    if (wb == 0) return true;
+    return na * (unsigned __int128)wb > nb * (unsigned __int128)wa;
+}
+
+__device__ void den_quota(int K, const uint32_t *celln_in, const unsigned long long *cellw, int *quota_out)
+{
+    int64_t celln[kDenCells], q[kDenCells], rem[kDenCells];
+    int fixed[kDenCells];
+    for (int c = 0; c < kDenCells; ++c) {
+        celln[c] = celln_in[c];
+        fixed[c] = 0;
+    }
+    for (;;) {
+        int64_t seats = K;
+        unsigned long long wa = 0;
+        for (int c = 0; c < kDenCells; ++c) {
+            if (fixed[c]) seats -= celln[c];
+            else if (celln[c] > 0) wa += cellw[c];
+        }
+        int64_t given = 0;
+        for (int c = 0; c < kDenCells; ++c) {
+            q[c] = 0;
+            rem[c] = -1;
+            if (fixed[c]) {
+                q[c] = celln[c];
+            } else if (celln[c] > 0 && wa > 0) {
+                const unsigned long long num = (unsigned long long)seats * cellw[c];
+                q[c] = (int64_t)(num / wa);
+                rem[c] = (int64_t)(num % wa);
+                given += q[c];
+            }
+        }
+        for (int64_t left = seats - given; left > 0; --left) {
+            int arg = -1;
+            for (int c = 0; c < kDenCells; ++c)
+                if (rem[c] >= 0 && (arg < 0 || rem[c] > rem[arg])) arg = c;
+            q[arg] += 1;
+            rem[arg] = -1;
+        }
+        int grew = 0;
+        for (int c = 0; c < kDenCells; ++c) {
+            if (!fixed[c] && q[c] > celln[c]) {
+                fixed[c] = 1;
+                grew = 1;
+            }
+        }
+        if (!grew) break;
+    }
+    int off = 0;
+    for (int c = 0; c < kDenCells; ++c) {
+        quota_out[c] = (int)q[c];
+        quota_out[kDenCells + c] = off;
+        off += (int)q[c];
+    }
+}
+
+__device__ void lbg_split(int K, int m, double eps, const unsigned long long *cs, double *centers)
+{
+    const int split = (2 * m <= K) ? m : K - m;
+    bool chosen[kMaxK];
+    for (int j = 0; j < m; ++j) chosen[j] = split == m;
+    if (split < m) {
+        for (int t = 0; t < split; ++t) {
+            int arg = -1;
+            unsigned __int128 na = 0;
+            unsigned long long wa = 0;
+            for (int k = 0; k < m; ++k) {
+                if (chosen[k]) continue;
+                const unsigned long long W = cs[5 * k + 3];
+                unsigned __int128 s2 = 0;
+                for (int ch = 0; ch < 3; ++ch) s2 += (unsigned __int128)cs[5 * k + ch] * cs[5 * k + ch];
+                const unsigned __int128 num = (unsigned __int128)W * cs[5 * k + 4] - s2;
+                if (arg < 0 || sse_greater(num, W, na, wa)) {
+                    arg = k;
+                    na = num;
+                    wa = W;
+                }
+            }
+            chosen[arg] = true;
+        }
+    }
+    int q = 0;
+    for (int j = 0; j < m; ++j) {
+        if (!chosen[j]) continue;
+        for (int ch = 0; ch < 3; ++ch) {
+            const double base = centers[3 * j + ch];
+            centers[3 * (m + q) + ch] = base + eps;
+            centers[3 * j + ch] = base - eps;
+        }
+        ++q;
+    }
+}
+
+// One block of any size (a multiple of 32, at most 1024 threads); `smem` holds
+// 2 * kMapSlots + 2 * kSffMax words.  Requires n > K.
+__device__ void sff_block(const uint32_t *keys, int64_t n, int K, uint64_t seed, int s0, double *centers,
+                          uint32_t *smem)
+{
+    __shared__ unsigned long long s_red[32];
+    __shared__ uint32_t s_cur;
+    const int nt = blockDim.x;
+    const uint32_t s = (uint32_t)(s0 < n ? s0 : n);
+    FyMap m{smem, smem + kMapSlots, kMapSlots - 1};
+    uint32_t *sub = smem + 2 * kMapSlots;   // kSffMax entries
+    uint32_t *mind = sub + kSffMax;         // kSffMax entries
+    clear_map(m.pos1, kMapSlots);
+    __syncthreads();
+    if (threadIdx.x == 0) fisher_yates((uint32_t)n, s, seed, 4, m, sub);
+    __syncthreads();
+    for (uint32_t i = s + threadIdx.x; i < kSffMax; i += nt) sub[i] = 0xFFFFFFFFu;
+    __syncthreads();
+    // bitonic sort of kSffMax entries, ascending
+    for (int size = 2; size <= kSffMax; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < kSffMax; i += nt) {
+                const int j = i ^ stride;
+                if (j > i) {
+                    const bool up = (i & size) == 0;
+                    const uint32_t a = sub[i], b = sub[j];
+                    if ((a > b) == up) {
+                        sub[i] = b;
+                        sub[j] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (threadIdx.x == 0) s_cur = (uint32_t)below(rand64(seed, 5, 0), (uint64_t)s);
+    __syncthreads();
+    uint32_t cur = s_cur;
+    if (threadIdx.x == 0) key_to_centre(centers, keys[sub[cur]]);
+    for (int k = 1; k < K; ++k) {
+        const uint32_t ck = keys[sub[cur]];
+        unsigned long long best = 0ull;
+        for (uint32_t i = threadIdx.x; i < s; i += nt) {
+            const uint32_t d = key_dist2(keys[sub[i]], ck);
+            const uint32_t md = (k == 1) ? d : min(mind[i], d);
+            mind[i] = md;
+            const unsigned long long packed = ((unsigned long long)md << 32) | (0xFFFFFFFFu - i);
+            best = packed > best ? packed : best;
+        }
+        for (int o = 16; o; o >>= 1) {
+            const unsigned long long other = __shfl_down_sync(kSeedFull, best, o);
+            best = other > best ? other : best;
+        }
+        if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = best;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long b = 0ull;
+            for (int wv = 0; wv < nt / 32; ++wv) b = s_red[wv] > b ? s_red[wv] : b;
+            s_cur = 0xFFFFFFFFu - (uint32_t)(b & 0xFFFFFFFFull);
+            key_to_centre(centers + 3 * k, keys[sub[s_cur]]);
+        }
+        __syncthreads();
+        cur = s_cur;
+    }
+}
+
+// Warp-level: index of the element of rank `j` (0-based, in key order) among the
+// unique colours whose class (channel value or cell) equals `cls`.
+// The unique list is cut into `nchunks` (a multiple of 32) chunks of
+// ceil(n / nchunks) colours; chunk_cnt[c * width + col] counts class `col` in chunk c.
+__device__ int64_t warp_locate(const uint32_t *keys, int64_t n, const uint32_t *chunk_cnt, int nchunks, int width,
+                               int col, uint32_t j, int mode, int ch)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t len = (n + nchunks - 1) / nchunks;
+    // chunk holding the element
+    uint32_t run = 0;
+    int cstar = nchunks - 1;
+    for (int base = 0; base < nchunks; base += 32) {
+        const uint32_t v = chunk_cnt[(size_t)(base + lane) * width + col];
+        uint32_t x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kSeedFull, x, o);
+            if (lane >= o) x += y;
+        }
+        const unsigned bal = __ballot_sync(kSeedFull, run + x > j);
+        if (bal) {
+            const int l = __ffs(bal) - 1;
+            cstar = base + l;
+            run += __shfl_sync(kSeedFull, x, l) - __shfl_sync(kSeedFull, v, l);
+            break;
+        }
+        run += __shfl_sync(kSeedFull, x, 31);
+    }
+    uint32_t r = j - run;
+    const int64_t lo = (int64_t)cstar * len, hi = lo + len < n ? lo + len : n;
+    for (int64_t base = lo; base < hi; base += 32) {
+        const int64_t i = base + lane;
+        bool match = false;
+        if (i < hi) {
+            const uint32_t key = keys[i];
+            match = mode == 0 ? (int)((key >> (16 - 8 * ch)) & 255u) == col - ch * 256 : den_cell(key) == col;
+        }
+        const unsigned bal = __ballot_sync(kSeedFull, match);
+        const uint32_t c = __popc(bal);
+        if (r < c) {
+            unsigned m = bal;
+            for (uint32_t q = 0; q < r; ++q) m &= m - 1;
+            return base + (__ffs(m) - 1);
+        }
+        r -= c;
+    }
+    return hi > 0 ? hi - 1 : 0;  // unreachable with consistent counts
+}
+
+
+// ---------------------------------------------------------------- VAR
+// Channel of largest pixel-weighted variance, compared exactly as W S2 - S1^2
+// (ties to the lower channel).
+__device__ __forceinline__ int var_channel(unsigned long long w, const unsigned long long *s1,
+                                           const unsigned long long *s2)
+{
+    const unsigned __int128 W = w;
+    int ch = 0;
+    unsigned __int128 best = 0;
+    for (int c = 0; c < 3; ++c) {
+        const unsigned __int128 a = s1[c], b = s2[c];
+        const unsigned __int128 v = W * b - a * a;
+        if (c == 0 || v > best) {
+            best = v;
+            ch = c;
+        }
+    }
+    return ch;
+}
+
+// Warp-level: centre g is the middle element (rank floor((lo + hi - 1) / 2)) of
+// group g = [g N' / K, (g + 1) N' / K) of the colours sorted by (channel value,
+// key); gcnt[ch * 256 + v] counts the colours whose channel value is v.
+__device__ void var_pick_warp(const uint32_t *keys, int64_t n, int K, int g, int ch, const uint32_t *chunk_cnt,
+                              int nchunks, const uint32_t *gcnt, double *centers)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t glo = (int64_t)g * n / K, ghi = (int64_t)(g + 1) * n / K;
+    const uint32_t m = (uint32_t)((glo + ghi - 1) / 2);
+    uint32_t run = 0;
+    int v = 255;
+    for (int base = 0; base < 256; base += 32) {
+        const uint32_t cv = gcnt[ch * 256 + base + lane];
+        uint32_t x = cv;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kSeedFull, x, o);
+            if (lane >= o) x += y;
+        }
+        const unsigned bal = __ballot_sync(kSeedFull, run + x > m);
+        if (bal) {
+            const int l = __ffs(bal) - 1;
+            v = base + l;
+            run += __shfl_sync(kSeedFull, x, l) - __shfl_sync(kSeedFull, cv, l);
+            break;
+        }
+        run += __shfl_sync(kSeedFull, x, 31);
+    }
+    const int64_t idx = warp_locate(keys, n, chunk_cnt, nchunks, 3 * 256, ch * 256 + v, m - run, 0, ch);
+    if (lane == 0) key_to_centre(centers + 3 * g, keys[idx]);
+}
+
+}  // namespace
+}  // namespace kq

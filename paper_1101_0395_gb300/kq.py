@@ -29,6 +29,20 @@ STATS_DTYPE = np.dtype([("iters", "<i4"), ("converged", "<i4"), ("k_eff", "<i4")
 STATS_BYTES = STATS_DTYPE.itemsize  # 40
 
 
+# kq_batch_item / kq_batch_result, field for field (LP64 layout)
+BATCH_ITEM_DTYPE = np.dtype([
+    ("rgb", "<u8"), ("idx", "<u8"), ("keys", "<u8"), ("weights", "<u8"), ("labels", "<u8"), ("scratch", "<u8"),
+    ("centers", "<u8"), ("palette", "<u8"), ("result", "<u8"), ("n_pixels", "<i8"), ("seed", "<u8"),
+    ("eps", "<f8"), ("lbg_eps", "<f8"), ("lbg_conv_eps", "<f8"), ("lbg_max_iter", "<i4"), ("K", "<i4"),
+    ("scheme", "<i4"), ("max_iter", "<i4"), ("capacity", "<i4"), ("reserved", "<i4")], align=True)
+BATCH_RESULT_DTYPE = np.dtype([("status", "<i4"), ("n_unique", "<i4"), ("lloyd", STATS_DTYPE),
+                               ("sse_num", "<i8")], align=True)
+
+
+class BatchConfig(C.Structure):
+    _fields_ = [("cluster", C.c_int32), ("reserved", C.c_int32), ("split_pixels", C.c_int64)]
+
+
 class KqError(RuntimeError):
     def __init__(self, fn: str, status: int):
         super().__init__("%s failed: %s (%d)" % (fn, strerror(status), status))
@@ -56,6 +70,13 @@ _SIGS = {
     "kq_status_read": (C.c_int, [_vp, C.POINTER(C.c_int32), _vp]),
     "kq_status_clear": (C.c_int, [_vp, _vp]),
     "kq_strerror": (C.c_char_p, [C.c_int]),
+    "kq_batch_scratch_bytes": (C.c_size_t, [C.c_int32]),
+    "kq_batch_workspace_size": (C.c_size_t, []),
+    "kq_batch_max_cluster": (C.c_int32, []),
+    "kq_batch_plan": (C.c_int, [_vp, C.c_int32, _vp, _vp, C.POINTER(C.c_int32)]),
+    "kq_batch_run": (C.c_int, [_vp, C.c_int32, _vp, C.c_int32, _vp, _vp, C.c_size_t, _vp]),
+    "kq_batch_tune": (C.c_int, [_vp, _vp, C.c_int32, _vp, _vp, C.POINTER(C.c_int32), C.POINTER(C.c_float), _vp,
+                                C.c_size_t, _vp]),
 }
 
 
@@ -252,6 +273,177 @@ class Quantizer:
                           + launches("kq_map", n))
         return Result(idx=idx, palette=pal.view(K, 3), centers=c.view(K, 3), n_unique=self.n_unique,
                       sse_num=self.sse_num, stats=self.stats)
+
+
+def kq_batch_scratch_bytes(capacity: int) -> int:
+    return int(lib().kq_batch_scratch_bytes(int(capacity)))
+
+
+def kq_batch_workspace_size() -> int:
+    return int(lib().kq_batch_workspace_size())
+
+
+def kq_batch_max_cluster() -> int:
+    return int(lib().kq_batch_max_cluster())
+
+
+def kq_batch_plan(h_items: np.ndarray, cfg: BatchConfig):
+    """Host planner: (order as int32 numpy array, n_big)."""
+    h_items = np.ascontiguousarray(h_items, dtype=BATCH_ITEM_DTYPE)
+    n = h_items.shape[0]
+    order = np.zeros(max(n, 1), dtype=np.int32)
+    nb = C.c_int32(0)
+    _check("kq_batch_plan", lib().kq_batch_plan(h_items.ctypes.data, n, C.byref(cfg), order.ctypes.data,
+                                                C.byref(nb)))
+    return order[:n], int(nb.value)
+
+
+def kq_batch_run(items: torch.Tensor, n_items: int, order: torch.Tensor, n_big: int, cfg: BatchConfig,
+                 ws: torch.Tensor, stream=None) -> None:
+    _check("kq_batch_run", lib().kq_batch_run(_ptr(items), int(n_items), _ptr(order), int(n_big), C.byref(cfg),
+                                              _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)))
+
+
+def kq_batch_tune(h_items: np.ndarray, items: torch.Tensor, order: torch.Tensor, ws: torch.Tensor, stream=None):
+    """Autotuner: (best BatchConfig, n_big, ms); `order` receives the best order."""
+    h_items = np.ascontiguousarray(h_items, dtype=BATCH_ITEM_DTYPE)
+    cfg = BatchConfig()
+    nb = C.c_int32(0)
+    ms = C.c_float(0.0)
+    _check("kq_batch_tune", lib().kq_batch_tune(h_items.ctypes.data, _ptr(items), h_items.shape[0], _ptr(order),
+                                                C.byref(cfg), C.byref(nb), C.byref(ms), _ptr(ws),
+                                                ws.numel() * ws.element_size(), _stream(stream)))
+    return cfg, int(nb.value), float(ms.value)
+
+
+def _align(v: int, a: int = 256) -> int:
+    return (v + a - 1) // a * a
+
+
+class BatchQuantizer:
+    """A batch of images quantized by one persistent launch (kq_batch_run).
+
+    All per-image buffers live in one device arena; ``rgb(i)`` is where image i's
+    pixels go, ``run()`` enqueues the batch on the current stream (no host
+    synchronisation) and ``capture()`` records it as a CUDA graph that ``replay()``
+    launches.
+    """
+
+    def __init__(self, n_pixels, Ks, schemes="KPP", seeds=0, eps: float = 1e-4, max_iter: int = 100,
+                 lbg_eps: float = 1.0, capacities=None, device=None):
+        dev = torch.device("cuda") if device is None else torch.device(device)
+        self.device = dev
+        n = len(n_pixels)
+        self.n_items = n
+        Ks = list(Ks) if not isinstance(Ks, int) else [Ks] * n
+        schemes = [schemes] * n if isinstance(schemes, str) else list(schemes)
+        seeds = [seeds] * n if isinstance(seeds, int) else list(seeds)
+        caps = [max(0, min(int(p), 1 << 24)) for p in n_pixels] if capacities is None else list(capacities)
+        self.n_pixels = [int(p) for p in n_pixels]
+        self.Ks = [int(k) for k in Ks]
+        self.capacity = caps
+        lay = []
+        off = 0
+        for i in range(n):
+            d = {}
+            for name, size in (("rgb", 3 * self.n_pixels[i]), ("idx", self.n_pixels[i]), ("keys", 4 * caps[i]),
+                               ("weights", 4 * caps[i]), ("labels", caps[i]),
+                               ("scratch", kq_batch_scratch_bytes(caps[i])), ("centers", 24 * self.Ks[i]),
+                               ("palette", 3 * self.Ks[i]), ("result", BATCH_RESULT_DTYPE.itemsize)):
+                d[name] = (off, size)
+                off = _align(off + max(size, 1))
+            lay.append(d)
+        self.layout = lay
+        self.arena = torch.zeros(max(off, 256), dtype=torch.uint8, device=dev)
+        base = self.arena.data_ptr()
+        items = np.zeros(n, dtype=BATCH_ITEM_DTYPE)
+        for i in range(n):
+            for name in ("rgb", "idx", "keys", "weights", "labels", "scratch", "centers", "palette", "result"):
+                items[i][name] = base + lay[i][name][0]
+            items[i]["n_pixels"] = self.n_pixels[i]
+            items[i]["seed"] = int(seeds[i]) & ((1 << 64) - 1)
+            items[i]["eps"] = eps
+            items[i]["lbg_eps"] = lbg_eps
+            items[i]["lbg_conv_eps"] = eps
+            items[i]["lbg_max_iter"] = max_iter
+            items[i]["K"] = self.Ks[i]
+            items[i]["scheme"] = INIT[schemes[i]] if isinstance(schemes[i], str) else int(schemes[i])
+            items[i]["max_iter"] = max_iter
+            items[i]["capacity"] = caps[i]
+        self.h_items = items
+        self.items = torch.from_numpy(items.view(np.uint8).copy()).to(dev)
+        self.order = torch.zeros(max(n, 1), dtype=torch.int32, device=dev)
+        self.ws = torch.zeros(kq_batch_workspace_size(), dtype=torch.uint8, device=dev)
+        self.cfg = BatchConfig(1, 0, 0)
+        self.n_big = 0
+        self.plan(self.cfg)
+        self.graph = None
+
+    def _view(self, i: int, name: str) -> torch.Tensor:
+        off, size = self.layout[i][name]
+        return self.arena[off:off + size]
+
+    def rgb(self, i: int) -> torch.Tensor:
+        return self._view(i, "rgb")
+
+    def idx(self, i: int) -> torch.Tensor:
+        return self._view(i, "idx")
+
+    def keys(self, i: int) -> torch.Tensor:
+        return self._view(i, "keys").view(torch.int32)
+
+    def weights(self, i: int) -> torch.Tensor:
+        return self._view(i, "weights").view(torch.int32)
+
+    def labels(self, i: int) -> torch.Tensor:
+        return self._view(i, "labels")
+
+    def centers(self, i: int) -> torch.Tensor:
+        return self._view(i, "centers").view(torch.float64).view(-1, 3)
+
+    def palette(self, i: int) -> torch.Tensor:
+        return self._view(i, "palette").view(-1, 3)
+
+    def results(self) -> np.ndarray:
+        """Every item's kq_batch_result (synchronizes)."""
+        out = np.zeros(self.n_items, dtype=BATCH_RESULT_DTYPE)
+        for i in range(self.n_items):
+            raw = self._view(i, "result").cpu().numpy().tobytes()
+            out[i] = np.frombuffer(raw, dtype=BATCH_RESULT_DTYPE)[0]
+        return out
+
+    def plan(self, cfg: BatchConfig) -> None:
+        order, nb = kq_batch_plan(self.h_items, cfg)
+        if self.n_items:
+            self.order[:self.n_items].copy_(torch.from_numpy(order))
+        self.cfg, self.n_big = cfg, nb
+        self.graph = None
+
+    def tune(self, stream=None) -> float:
+        cfg, nb, ms = kq_batch_tune(self.h_items, self.items, self.order, self.ws, stream=stream)
+        self.cfg, self.n_big = cfg, nb
+        self.graph = None
+        return ms
+
+    def run(self, stream=None) -> None:
+        kq_batch_run(self.items, self.n_items, self.order, self.n_big, self.cfg, self.ws, stream=stream)
+
+    def capture(self) -> None:
+        """Records run() in a CUDA graph (one memset node and one kernel node)."""
+        s = torch.cuda.Stream(device=self.device)
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.run()
+        torch.cuda.current_stream().wait_stream(s)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.run()
+        self.graph = g
+
+    def replay(self) -> None:
+        if self.graph is None:
+            self.capture()
+        self.graph.replay()
 
 
 def exported_symbols() -> list:

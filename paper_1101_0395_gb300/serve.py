@@ -1,0 +1,337 @@
+"""Serving: a request loop with memory admission and continuous batching.
+
+Requests (one image each, with its own K, scheme and seed) arrive over time.
+The server keeps on the device
+
+* a pool of device memory from which each admitted request gets one block
+  (its pixels, its unique colours and weights, labels, seeding scratch, centres,
+  palette, result and output indices: ``request_bytes``), and
+* ``streams`` batch workspaces (kq_batch_workspace_size each), whose colour
+  tables stay resident and zero between requests.
+
+``step()`` is the scheduler.  It retires every wave whose completion event has
+fired (freeing its requests' blocks and its workspace), then, while a workspace
+is free and requests are waiting, forms a wave: requests are taken in arrival
+order as long as their blocks fit in the pool (memory admission; the first that
+does not fit waits, so no request is overtaken), their pixels are copied in,
+and the wave runs as one kq_batch_run on its own stream, followed by the copies
+of the results to the host.  A wave started while another is still running
+overlaps with it on the device: the running launch's persistent blocks leave
+as its queue empties and the new launch's blocks take their SMs.  Each image is
+computed by one block group with no data shared with other images, so a
+request's result does not depend on what else is in the batch.
+
+The device side sits behind a small backend interface so that the scheduling
+logic can be exercised without a GPU.
+"""
+from __future__ import annotations
+
+import time
+from collections import deque
+from dataclasses import dataclass, field
+from typing import Deque, Dict, List, Optional, Tuple
+
+import numpy as np
+
+ALIGN = 256
+
+
+def _align(v: int, a: int = ALIGN) -> int:
+    return (v + a - 1) // a * a
+
+
+class Arena:
+    """First-fit allocator over [0, size) with 256-byte alignment (offsets only)."""
+
+    def __init__(self, size: int):
+        self.size = int(size)
+        self.free: List[Tuple[int, int]] = [(0, self.size)]  # (offset, length), sorted, coalesced
+        self.used: Dict[int, int] = {}
+        self.in_use = 0
+        self.peak = 0
+
+    def alloc(self, nbytes: int) -> Optional[int]:
+        n = _align(max(int(nbytes), 1))
+        for j, (off, ln) in enumerate(self.free):
+            if ln >= n:
+                if ln == n:
+                    self.free.pop(j)
+                else:
+                    self.free[j] = (off + n, ln - n)
+                self.used[off] = n
+                self.in_use += n
+                self.peak = max(self.peak, self.in_use)
+                return off
+        return None
+
+    def release(self, off: int) -> None:
+        n = self.used.pop(off)
+        self.in_use -= n
+        self.free.append((off, n))
+        self.free.sort()
+        merged: List[Tuple[int, int]] = []
+        for o, ln in self.free:
+            if merged and merged[-1][0] + merged[-1][1] == o:
+                merged[-1] = (merged[-1][0], merged[-1][1] + ln)
+            else:
+                merged.append((o, ln))
+        self.free = merged
+
+
+def request_layout(n_pixels: int, K: int, scratch_bytes) -> Tuple[Dict[str, Tuple[int, int]], int]:
+    """Offsets (relative to a request's block) and sizes of its device buffers."""
+    cap = max(0, min(int(n_pixels), 1 << 24))
+    lay: Dict[str, Tuple[int, int]] = {}
+    off = 0
+    for name, size in (("rgb", 3 * n_pixels), ("idx", n_pixels), ("keys", 4 * cap), ("weights", 4 * cap),
+                       ("labels", cap), ("scratch", scratch_bytes(cap)), ("centers", 24 * K),
+                       ("palette", 3 * K), ("result", 56)):
+        lay[name] = (off, size)
+        off = _align(off + max(size, 1))
+    return lay, off
+
+
+@dataclass
+class Request:
+    rid: int
+    rgb: object                # host pixels, n_pixels x 3 uint8: numpy array or (pinned) torch CPU tensor
+    K: int
+    scheme: str = "KPP"
+    seed: int = 0
+    eps: float = 1e-4
+    max_iter: int = 100
+    arrival: float = 0.0       # seconds on the server's clock
+    # filled in by the server
+    n_pixels: int = 0
+    block: int = -1
+    layout: Dict[str, Tuple[int, int]] = field(default_factory=dict)
+    nbytes: int = 0
+    admitted: float = -1.0
+    done: float = -1.0
+    idx: Optional[np.ndarray] = None
+    palette: Optional[np.ndarray] = None
+    centers: Optional[np.ndarray] = None
+    result: Optional[np.ndarray] = None
+
+
+@dataclass
+class Wave:
+    slot: int
+    requests: List[Request]
+    handle: object = None
+
+
+class Server:
+    """Continuous-batching quantization server (see the module docstring)."""
+
+    def __init__(self, backend, pool_bytes: int, streams: int = 2, max_wave: int = 64, clock=time.perf_counter):
+        self.backend = backend
+        self.arena = Arena(pool_bytes)
+        self.streams = int(streams)
+        self.max_wave = int(max_wave)
+        self.clock = clock
+        self.t0 = clock()
+        backend.setup(pool_bytes, self.streams, self.max_wave)
+        self.free_slots: Deque[int] = deque(range(self.streams))
+        self.waiting: Deque[Request] = deque()
+        self.running: List[Wave] = []
+        self.finished: List[Request] = []
+        self.waves = 0
+
+    def now(self) -> float:
+        return self.clock() - self.t0
+
+    def submit(self, req: Request) -> None:
+        npx = req.rgb.numel() if hasattr(req.rgb, "numel") else req.rgb.size
+        req.n_pixels = int(npx // 3)
+        req.layout, req.nbytes = request_layout(req.n_pixels, req.K, self.backend.scratch_bytes)
+        if req.nbytes > self.arena.size:
+            raise ValueError("request %d needs %d bytes, more than the whole pool" % (req.rid, req.nbytes))
+        self.waiting.append(req)
+
+    def step(self) -> int:
+        """Retires finished waves and launches new ones; returns requests completed."""
+        done = 0
+        still: List[Wave] = []
+        for wv in self.running:
+            if self.backend.done(wv.handle):
+                t = self.now()
+                self.backend.collect(wv.handle, wv.requests)
+                for r in wv.requests:
+                    r.done = t
+                    self.arena.release(r.block)
+                    self.finished.append(r)
+                done += len(wv.requests)
+                self.free_slots.append(wv.slot)
+            else:
+                still.append(wv)
+        self.running = still
+        while self.free_slots and self.waiting:
+            batch: List[Request] = []
+            while self.waiting and len(batch) < self.max_wave:
+                r = self.waiting[0]
+                off = self.arena.alloc(r.nbytes)
+                if off is None:
+                    break  # waits for memory; nothing behind it is admitted first
+                self.waiting.popleft()
+                r.block = off
+                r.admitted = self.now()
+                batch.append(r)
+            if not batch:
+                break
+            slot = self.free_slots.popleft()
+            handle = self.backend.launch(slot, batch)
+            self.running.append(Wave(slot, batch, handle))
+            self.waves += 1
+        return done
+
+    def idle(self) -> bool:
+        return not self.waiting and not self.running
+
+    def drain(self, poll_s: float = 0.0) -> None:
+        while not self.idle():
+            if self.step() == 0 and poll_s > 0:
+                time.sleep(poll_s)
+
+
+def run_trace(server: Server, requests: List[Request], poll_s: float = 0.0002) -> Dict:
+    """Submits each request at its arrival time (server clock), runs the
+    scheduler until all are done, and summarises latency and throughput."""
+    reqs = sorted(requests, key=lambda r: r.arrival)
+    server.t0 = server.clock()
+    i = 0
+    while i < len(reqs) or not server.idle():
+        t = server.now()
+        while i < len(reqs) and reqs[i].arrival <= t:
+            server.submit(reqs[i])
+            i += 1
+        if server.step() == 0:
+            nxt = reqs[i].arrival - server.now() if i < len(reqs) else poll_s
+            if nxt > 0:
+                time.sleep(min(poll_s, nxt))
+    return summarize(reqs)
+
+
+def summarize(reqs: List[Request]) -> Dict:
+    lat = np.array([r.done - r.arrival for r in reqs], dtype=np.float64)
+    span = max(r.done for r in reqs) - min(r.arrival for r in reqs) if reqs else 0.0
+    px = sum(r.n_pixels for r in reqs)
+    return {"requests": len(reqs), "p50_ms": float(np.percentile(lat, 50) * 1e3) if reqs else 0.0,
+            "p99_ms": float(np.percentile(lat, 99) * 1e3) if reqs else 0.0,
+            "mean_ms": float(lat.mean() * 1e3) if reqs else 0.0,
+            "img_per_s": len(reqs) / span if span > 0 else 0.0, "mpix_per_s": px / span / 1e6 if span > 0 else 0.0,
+            "span_s": span}
+
+
+def poisson_arrivals(rate: float, duration: float, seed: int) -> np.ndarray:
+    """Arrival times of a Poisson process (exponential gaps from SplitMix64 uniforms)."""
+    from . import synth
+
+    n_max = int(rate * duration * 1.5 + 64)
+    u = synth.uniform(seed, 30, n_max)
+    t = np.cumsum(-np.log1p(-u) / rate)
+    return t[t < duration]
+
+
+class CudaBackend:
+    """The device side of the server: one pool tensor, `streams` workspaces, item
+    buffers and pinned staging buffers, and one kq_batch_run per wave."""
+
+    OUT = ("idx", "palette", "centers", "result")
+
+    def __init__(self, cluster: int = 1, split_pixels: int = 1 << 62, device=None):
+        import torch
+
+        from . import kq
+
+        self.torch, self.kq = torch, kq
+        self.device = torch.device("cuda") if device is None else torch.device(device)
+        self.cfg = kq.BatchConfig(int(cluster), 0, int(split_pixels))
+
+    def scratch_bytes(self, cap: int) -> int:
+        return self.kq.kq_batch_scratch_bytes(cap)
+
+    def setup(self, pool_bytes: int, streams: int, max_wave: int) -> None:
+        torch, kq = self.torch, self.kq
+        self.pool = torch.empty(pool_bytes, dtype=torch.uint8, device=self.device)
+        wsb = kq.kq_batch_workspace_size()
+        self.ws = [torch.zeros(wsb, dtype=torch.uint8, device=self.device) for _ in range(streams)]
+        isz = kq.BATCH_ITEM_DTYPE.itemsize
+        self.items = [torch.empty(max_wave * isz, dtype=torch.uint8, device=self.device) for _ in range(streams)]
+        self.order = [torch.empty(max_wave, dtype=torch.int32, device=self.device) for _ in range(streams)]
+        self.h_items = [torch.empty(max_wave * isz, dtype=torch.uint8).pin_memory() for _ in range(streams)]
+        self.h_order = [torch.empty(max_wave, dtype=torch.int32).pin_memory() for _ in range(streams)]
+        self.h_out = [torch.empty(1 << 20, dtype=torch.uint8).pin_memory() for _ in range(streams)]
+        self.streams = [torch.cuda.Stream(device=self.device) for _ in range(streams)]
+        self.events = [torch.cuda.Event() for _ in range(streams)]
+        self.h2d_bytes = 0
+        self.d2h_bytes = 0
+
+    def _pinned(self, r: "Request"):
+        t = r.rgb
+        if isinstance(t, np.ndarray):
+            t = self.torch.from_numpy(np.ascontiguousarray(t).reshape(-1))
+        return t.reshape(-1)
+
+    def launch(self, slot: int, batch: List[Request]):
+        torch, kq = self.torch, self.kq
+        s = self.streams[slot]
+        base = self.pool.data_ptr()
+        items = np.zeros(len(batch), dtype=kq.BATCH_ITEM_DTYPE)
+        need = sum(_align(r.layout[n][1]) for r in batch for n in self.OUT)
+        if need > self.h_out[slot].numel():
+            self.h_out[slot] = torch.empty(_align(need * 2, 1 << 20), dtype=torch.uint8).pin_memory()
+        stage = self.h_out[slot]
+        outs = []
+        with torch.cuda.stream(s):
+            for j, r in enumerate(batch):
+                b = r.block
+                for name in ("rgb", "idx", "keys", "weights", "labels", "scratch", "centers", "palette", "result"):
+                    items[j][name] = base + b + r.layout[name][0]
+                cap = max(0, min(r.n_pixels, 1 << 24))
+                items[j]["n_pixels"], items[j]["seed"], items[j]["eps"] = r.n_pixels, r.seed, r.eps
+                items[j]["lbg_eps"], items[j]["lbg_conv_eps"], items[j]["lbg_max_iter"] = 1.0, r.eps, r.max_iter
+                items[j]["K"], items[j]["scheme"] = r.K, kq.INIT[r.scheme]
+                items[j]["max_iter"], items[j]["capacity"] = r.max_iter, cap
+                off, size = r.layout["rgb"]
+                if size:
+                    self.pool[b + off:b + off + size].copy_(self._pinned(r), non_blocking=True)
+                    self.h2d_bytes += size
+            order, nb = kq.kq_batch_plan(items, self.cfg)
+            hi = self.h_items[slot][:items.nbytes]
+            hi.numpy()[:] = items.view(np.uint8)
+            self.items[slot][:items.nbytes].copy_(hi, non_blocking=True)
+            ho = self.h_order[slot][:len(batch)]
+            ho.numpy()[:] = order
+            self.order[slot][:len(batch)].copy_(ho, non_blocking=True)
+            kq.kq_batch_run(self.items[slot], len(batch), self.order[slot], nb, self.cfg, self.ws[slot], stream=s)
+            so = 0
+            for r in batch:
+                b = r.block
+                o = {}
+                for name in self.OUT:
+                    off, size = r.layout[name]
+                    if size:
+                        stage[so:so + size].copy_(self.pool[b + off:b + off + size], non_blocking=True)
+                        self.d2h_bytes += size
+                    o[name] = (so, size)
+                    so += _align(size)
+                outs.append(o)
+            ev = self.events[slot]
+            ev.record(s)
+        return (slot, ev, outs)
+
+    def done(self, handle) -> bool:
+        return handle[1].query()
+
+    def collect(self, handle, batch: List[Request]) -> None:
+        kq = self.kq
+        stage = self.h_out[handle[0]].numpy()
+        for r, o in zip(batch, handle[2]):
+            def get(name):
+                so, size = o[name]
+                return stage[so:so + size].copy()
+            r.idx = get("idx")
+            r.palette = get("palette").reshape(-1, 3)
+            r.centers = get("centers").view(np.float64).reshape(-1, 3)
+            r.result = np.frombuffer(get("result").tobytes(), dtype=kq.BATCH_RESULT_DTYPE)[0]

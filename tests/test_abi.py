@@ -3,6 +3,9 @@ symbol include/kq.h declares, and rejects invalid arguments before touching
 the device."""
 import ctypes as C
 
+import numpy as np
+import pytest
+
 from paper_1101_0395_gb300 import kq
 
 WS = C.c_void_p(1 << 20)  # aligned fake address: never dereferenced on these paths
@@ -11,7 +14,9 @@ WS = C.c_void_p(1 << 20)  # aligned fake address: never dereferenced on these pa
 def test_exports_every_declared_symbol():
     names = kq.exported_symbols()
     assert set(names) == {"kq_workspace_size", "kq_workspace_init", "kq_histogram", "kq_seed", "kq_lloyd", "kq_map",
-                          "kq_lloyd_noalloc", "kq_status_read", "kq_status_clear", "kq_strerror"}
+                          "kq_lloyd_noalloc", "kq_status_read", "kq_status_clear", "kq_strerror",
+                          "kq_batch_scratch_bytes", "kq_batch_workspace_size", "kq_batch_max_cluster",
+                          "kq_batch_plan", "kq_batch_run", "kq_batch_tune"}
     L = kq.lib()
     for n in names:
         assert getattr(L, n) is not None
@@ -59,3 +64,54 @@ def test_strerror():
     for code in (0, -1, -2, -3, -4, -5):
         assert kq.strerror(code) and kq.strerror(code) != "unknown status"
     assert kq.strerror(99) == "unknown status"
+
+
+def _fake_items(spec):
+    items = np.zeros(len(spec), dtype=kq.BATCH_ITEM_DTYPE)
+    for i, (n, K) in enumerate(spec):
+        for f in ("rgb", "idx", "keys", "weights", "labels", "scratch", "centers", "palette", "result"):
+            items[i][f] = (1 << 20) + 4096 * i  # never dereferenced by the planner
+        items[i]["n_pixels"], items[i]["K"], items[i]["scheme"] = n, K, 6
+        items[i]["max_iter"], items[i]["capacity"], items[i]["eps"] = 100, n, 1e-4
+        items[i]["lbg_max_iter"] = 100
+    return items
+
+
+def test_batch_structs_and_scratch():
+    assert kq.BATCH_ITEM_DTYPE.itemsize == 136 and kq.BATCH_RESULT_DTYPE.itemsize == 56
+    assert kq.kq_batch_scratch_bytes(1000) == 8192 + 16 * 32 + 256
+    assert kq.kq_batch_scratch_bytes(0) == 256 and kq.kq_batch_scratch_bytes(-1) == 0
+
+
+def test_batch_planner_orders_largest_work_first():
+    items = _fake_items([(100, 16), (5000, 256), (0, 8), (70000, 32)])
+    order, nb = kq.kq_batch_plan(items, kq.BatchConfig(1, 0, 0))
+    assert nb == 0 and list(order) == [3, 1, 0, 2]
+    order, nb = kq.kq_batch_plan(items, kq.BatchConfig(4, 0, 1000))
+    assert nb == 2 and list(order) == [3, 1, 0, 2]
+    order, nb = kq.kq_batch_plan(items, kq.BatchConfig(4, 0, 6000))
+    assert nb == 1 and list(order) == [3, 1, 0, 2]
+    for field, value in (("K", 0), ("K", 257), ("scheme", 8), ("max_iter", 0), ("n_pixels", -1),
+                         ("capacity", -1), ("keys", 0)):
+        bad = items.copy()
+        bad[1][field] = value
+        with pytest.raises(kq.KqError):
+            kq.kq_batch_plan(bad, kq.BatchConfig(1, 0, 0))
+    for cl in (0, 3, 32):
+        with pytest.raises(kq.KqError):
+            kq.kq_batch_plan(items, kq.BatchConfig(cl, 0, 0))
+
+
+def test_batch_run_rejects_bad_arguments_on_the_host():
+    L = kq.lib()
+    p = C.c_void_p(1 << 20)
+    cfg = kq.BatchConfig(1, 0, 0)
+    size = 1 << 30
+    assert L.kq_batch_run(p, 4, p, 5, C.byref(cfg), WS, size, None) == kq.KQ_EINVAL   # n_big > n_items
+    assert L.kq_batch_run(p, 4, p, 1, C.byref(cfg), WS, size, None) == kq.KQ_EINVAL   # clusters off, n_big > 0
+    assert L.kq_batch_run(p, 4, p, 0, C.byref(cfg), C.c_void_p((1 << 20) + 8), size, None) == kq.KQ_EINVAL
+    assert L.kq_batch_run(None, 4, p, 0, C.byref(cfg), WS, size, None) == kq.KQ_EINVAL
+    assert L.kq_batch_run(p, 4, p, 0, None, WS, size, None) == kq.KQ_EINVAL
+    bad = kq.BatchConfig(6, 0, 0)
+    assert L.kq_batch_run(p, 4, p, 0, C.byref(bad), WS, size, None) == kq.KQ_EINVAL
+    assert L.kq_batch_tune(None, p, 4, p, None, None, None, WS, size, None) == kq.KQ_EINVAL
