@@ -8,6 +8,8 @@ stream; between steps a 256 MiB buffer is written to flush the 129 MB L2 (not
 timed).  Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+  python bench.py --workload batched [--count 512]     # img/s, one launch per batch
+  python bench.py --workload serving [--rate 200]      # p50/p99 latency under Poisson arrivals
 
 Under torchrun (N > 1) every rank quantizes its own image (independent
 replicas, no data exchange); value = pixels of all ranks / max step time.
@@ -47,6 +49,9 @@ def parse_args(argv=None):
     p.add_argument("--workload", default=WORKLOAD)
     p.add_argument("--K", type=int, default=K_DEFAULT)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--count", type=int, default=512, help="batched: images per batch")
+    p.add_argument("--rate", type=float, default=200.0, help="serving: Poisson arrival rate (req/s)")
+    p.add_argument("--duration", type=float, default=10.0, help="serving: arrival trace length (s)")
     return p.parse_args(argv)
 
 
@@ -196,6 +201,260 @@ def workload_config(wl, img, K, n_unique=None, iters=None) -> dict:
     return cfg
 
 
+def _gen_batch_image(args):
+    from paper_1101_0395_gb300 import synth
+
+    h, w, seed = args
+    return synth.batch_image(h, w, seed)
+
+
+def batch_images(spec, workers=None):
+    """The batch's images, generated on all host cores (spawned workers, so no
+    CUDA state is ever forked)."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+
+    jobs = [(h, w, s) for (h, w), s in zip(spec.sizes, spec.seeds)]
+    with ProcessPoolExecutor(max_workers=workers or os.cpu_count(), mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_gen_batch_image, jobs, chunksize=1))
+
+
+def batched_config(spec, n_px, tuned=None) -> dict:
+    cfg = {"workload": "batched: %d synthetic RGB8 images, side log-uniform 64-2048, aspect 0.5-2, K from "
+                       "{16,32,64,128,256}, %s seeds, eps=1e-4, <=100 passes; one persistent launch per batch "
+                       "(CUDA graph)" % (len(spec.sizes), SCHEME),
+           "images": len(spec.sizes), "n_pixels": int(sum(n_px)), "l2": "inputs larger than L2 (no flush)",
+           "parallelism": "replicas (one batch per GPU)"}
+    if tuned is not None:
+        cfg["launch_shape"] = tuned
+    return cfg
+
+
+def run_batched(args, rank, world, local) -> None:
+    import numpy as np
+
+    from paper_1101_0395_gb300 import synth
+
+    spec = synth.batch_spec(args.count, seed=3101 + 7 * rank)
+    imgs = batch_images(spec)
+    import torch
+
+    from paper_1101_0395_gb300 import kq
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n_px = [im.size // 3 for im in imgs]
+    bq = kq.BatchQuantizer(n_px, spec.ks, SCHEME, spec.seeds, 1e-4, 100, device=dev)
+    h_rgb = [torch.from_numpy(im.reshape(-1)).pin_memory() for im in imgs]
+    for i in range(len(imgs)):
+        bq.rgb(i).copy_(h_rgb[i], non_blocking=True)
+    torch.cuda.synchronize()
+    tune_ms = bq.tune()
+    shape = {"cluster": bq.cfg.cluster, "split_pixels": bq.cfg.split_pixels, "images_on_clusters": bq.n_big,
+             "autotuned_ms": tune_ms}
+    bq.capture()
+    stream = torch.cuda.current_stream()
+    for _ in range(max(3, args.warmup)):
+        bq.replay()
+    torch.cuda.synchronize()
+    res = bq.results()
+    if np.any(res["status"] != kq.KQ_OK):
+        raise RuntimeError("batch item errors: %s" % np.unique(res["status"]))
+    steps = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    props = torch.cuda.get_device_properties(dev)
+    clocks = ClockSampler("GPU-%s" % props.uuid if getattr(props, "uuid", None) else str(local))
+    clocks.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    for s in range(steps):
+        ev[s][0].record(stream)
+        bq.replay()
+        ev[s][1].record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    ms = reduce_max(sum(a.elapsed_time(b) for a, b in ev) / steps, world)
+    n_img = len(imgs)
+    value = n_img * world / (ms * 1e-3)
+    res = bq.results()
+    t = res["t_ns"].astype(np.float64)
+    stage = np.diff(t, axis=1) / 1e6
+    big = np.zeros(n_img, bool)
+    big[bq.order[:bq.n_big].cpu().numpy()] = True
+    wgt = np.where(big, bq.cfg.cluster, 1)
+    cta_ms = {nm: float((stage[:, j] * wgt).sum()) for j, nm in enumerate(["histogram", "seed", "lloyd", "map"])}
+    # end to end: pixels in from pinned host memory, indices and results back
+    h_idx = [torch.empty(n, dtype=torch.uint8).pin_memory() for n in n_px]
+    e2e_steps = max(3, min(steps, 10))
+    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(e2e_steps)]
+    for s in range(e2e_steps):
+        e2e_ev[s][0].record(stream)
+        for i in range(n_img):
+            bq.rgb(i).copy_(h_rgb[i], non_blocking=True)
+        bq.replay()
+        for i in range(n_img):
+            h_idx[i].copy_(bq.idx(i), non_blocking=True)
+        e2e_ev[s][1].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = reduce_max(sum(a.elapsed_time(b) for a, b in e2e_ev) / e2e_steps, world)
+    # the plain per-image path on the same GPU and images
+    q = kq.Quantizer(max(n_px), device=dev)
+    sse_loop = []
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for rep in range(2):
+        sse_loop.clear()
+        a0.record(stream)
+        for i in range(n_img):
+            r = q.quantize(bq.rgb(i), spec.ks[i], SCHEME, spec.seeds[i], 1e-4, 100)
+            sse_loop.append(r.sse_num.clone())
+        a1.record(stream)
+        torch.cuda.synchronize()
+    loop_ms = a0.elapsed_time(a1)
+    sse_b = res["sse_num"].astype(np.int64)
+    sse_l = np.array([int(x.item()) for x in sse_loop], dtype=np.int64)
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz") or 2070.0)
+    fp32_peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    ndc = float(res["lloyd"]["ndc"].sum())
+    achieved = ndc * FLOP_PER_DIST / (ms * 1e-3) / 1e12
+    line = {"metric": "batched img/s", "value": value, "unit": "img/s", "n_gpus": world, "steps": steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": batched_config(spec, n_px, shape),
+            "clocks": {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+            "e2e": {"value": n_img * world / (e2e_ms * 1e-3), "unit": "img/s",
+                    "h2d_bytes_per_step": int(3 * sum(n_px)), "d2h_bytes_per_step": int(sum(n_px))},
+            "gpu_launches": steps,
+            "mpix_per_s": sum(n_px) * world / (ms * 1e-3) / 1e6,
+            "roofline": {"kernel": "batch_kernel (kq_batch_run)", "bound": "alu", "achieved": achieved,
+                         "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                         "algorithmic": "%d FLOP per distance x NDC summed over the batch (%.3g)"
+                                        % (FLOP_PER_DIST, ndc),
+                         "peak_source": "derived: SMs x 128 FP32 lanes x 2 FLOP x max SM clock"},
+            "stage_cta_ms": cta_ms,
+            "per_image_path": {"value": n_img / (loop_ms * 1e-3), "unit": "img/s", "ms": loop_ms,
+                               "same_sse_images": int((sse_b == sse_l).sum()),
+                               "mse_batched": float(sse_b.sum() / sum(n_px)),
+                               "mse_per_image": float(sse_l.sum() / sum(n_px))}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = batched_cpu_baseline(imgs, spec)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def batched_cpu_baseline(imgs, spec, budget_s: float = 15.0) -> dict:
+    """The oracle on a size-stratified sample of the batch (every 64th image by
+    size), as img/s at the batch's mean image size."""
+    import oracle
+
+    order = sorted(range(len(imgs)), key=lambda i: imgs[i].size)
+    sample = order[::max(1, len(order) // 8)]
+    px, t_total, done = 0, 0.0, 0
+    for i in sample:
+        t0 = time.perf_counter()
+        oracle.quantize(imgs[i], spec.ks[i], SCHEME, spec.seeds[i], 1e-4, 100)
+        t_total += time.perf_counter() - t0
+        px += imgs[i].size // 3
+        done += 1
+        if t_total > budget_s:
+            break
+    mean_px = sum(im.size // 3 for im in imgs) / len(imgs)
+    mpix = px / t_total / 1e6
+    return {"value": mpix * 1e6 / mean_px, "unit": "img/s", "cores": 1, "kind": "oracle",
+            "sample": "%d of %d images (stratified by size), %.1f Mpx in %.1f s = %.3f Mpix/s, at the batch's mean "
+                      "of %.0f px per image" % (done, len(imgs), px / 1e6, t_total, mpix, mean_px),
+            "cpu": cpu_model(), "nproc": os.cpu_count()}
+
+
+def serving_trace(args, seed=4101):
+    """Arrivals and request shapes: side log-uniform 256-4096 (aspect 0.5-2),
+    K uniform in 8..256; images come from a pool of 48 generated images."""
+    import numpy as np
+
+    from paper_1101_0395_gb300 import serve, synth
+
+    arrivals = serve.poisson_arrivals(args.rate, args.duration, seed)
+    pool = synth.batch_spec(48, side_lo=256, side_hi=4096, seed=seed, k_uniform_range=(8, 256))
+    u = synth.uniform(seed, 40, 2 * max(1, arrivals.size))
+    picks = (u[0::2] * len(pool.sizes)).astype(int)
+    ks = 8 + np.minimum(248, (u[1::2] * 249).astype(int))
+    return arrivals, pool, picks, ks
+
+
+def run_serving(args, rank, world, local) -> None:
+
+    arrivals, pool, picks, ks = serving_trace(args)
+    imgs = batch_images(pool)
+    import torch
+
+    from paper_1101_0395_gb300 import kq, serve
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    h_imgs = [torch.from_numpy(im.reshape(-1)).pin_memory() for im in imgs]
+    max_px = max(im.size // 3 for im in imgs)
+
+    def requests(count=None):
+        out = []
+        for i in range(arrivals.size if count is None else count):
+            j = int(picks[i])
+            out.append(serve.Request(rid=i, rgb=h_imgs[j], K=int(ks[i]), scheme=SCHEME, seed=1000 + i,
+                                     arrival=float(arrivals[i]) if count is None else 0.0))
+        return out
+
+    # launch shape: the autotuner on one wave-sized batch of the pool
+    n_px = [im.size // 3 for im in imgs]
+    bq = kq.BatchQuantizer(n_px, [int(k) for k in ks[:len(imgs)]], SCHEME, list(range(len(imgs))), device=dev)
+    for i in range(len(imgs)):
+        bq.rgb(i).copy_(h_imgs[i])
+    bq.tune()
+    cluster, split = bq.cfg.cluster, bq.cfg.split_pixels
+    del bq
+    torch.cuda.empty_cache()
+    pool_bytes = 48 << 30
+    props = torch.cuda.get_device_properties(dev)
+    clocks = ClockSampler("GPU-%s" % props.uuid if getattr(props, "uuid", None) else str(local))
+    srv = serve.Server(serve.CudaBackend(cluster, split, device=dev), pool_bytes, streams=2, max_wave=64)
+    srv.drain()
+    for r in requests(8):
+        srv.submit(r)
+    srv.drain()  # warm-up
+    srv.finished.clear()
+    clocks.start()
+    reqs = requests()
+    h2d0, d2h0 = srv.backend.h2d_bytes, srv.backend.d2h_bytes
+    out = serve.run_trace(srv, reqs)
+    clk = clocks.stop()
+    h2d, d2h = srv.backend.h2d_bytes - h2d0, srv.backend.d2h_bytes - d2h0
+    del srv
+    torch.cuda.empty_cache()
+    # the plain per-image path behind the same scheduler, on the same trace
+    plain = serve.Server(serve.PlainBackend(max_px, device=dev), 1 << 30, streams=1, max_wave=1)
+    preqs = requests()
+    pout = serve.run_trace(plain, preqs)
+    same = sum(int(a.result["sse_num"]) == int(b.result["sse_num"]) for a, b in zip(reqs, preqs))
+    line = {"metric": "serve p99 ms", "value": out["p99_ms"], "unit": "ms", "n_gpus": world, "steps": len(reqs),
+            "warmup": 8, "ms_per_step": out["mean_ms"], "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "serving: Poisson arrivals at %g req/s for %g s; image side log-uniform 256-4096 "
+                                   "(aspect 0.5-2, pool of 48 images), K uniform 8..256, %s seeds, eps=1e-4, "
+                                   "<=100 passes; memory-admitted continuous batching on 2 streams"
+                                   % (args.rate, args.duration, SCHEME),
+                       "requests": len(reqs), "launch_shape": {"cluster": cluster, "split_pixels": split},
+                       "pool_bytes": pool_bytes, "l2": "inputs larger than L2 (no flush)"},
+            "clocks": {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+            "e2e": {"value": out["p99_ms"], "unit": "ms", "h2d_bytes_per_step": int(h2d / max(1, len(reqs))),
+                    "d2h_bytes_per_step": int(d2h / max(1, len(reqs)))},
+            "gpu_launches": None,
+            "p50_ms": out["p50_ms"], "img_per_s": out["img_per_s"], "mpix_per_s": out["mpix_per_s"],
+            "per_image_path": {"p50_ms": pout["p50_ms"], "p99_ms": pout["p99_ms"], "img_per_s": pout["img_per_s"],
+                               "same_sse_requests": same}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_reference(args, rank, world) -> None:
     """The reference arm: the FP64 CPU oracle on the same workload."""
     if rank != 0:
@@ -203,6 +462,34 @@ def run_reference(args, rank, world) -> None:
     import oracle  # noqa: F401
     from paper_1101_0395_gb300 import synth
 
+    if args.workload == "serving":
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle is a batch program; it has no request "
+                                                              "loop to time under arrivals"}), flush=True)
+        return
+    if args.workload == "batched":
+        spec = synth.batch_spec(args.count)
+        order = sorted(range(len(spec.sizes)), key=lambda i: spec.sizes[i][0] * spec.sizes[i][1])
+        pick = order[::max(1, len(order) // 8)]
+        sub = synth.BatchSpec([spec.sizes[i] for i in pick], [spec.ks[i] for i in pick],
+                              [spec.seeds[i] for i in pick])
+        imgs = batch_images(sub)
+        mean_px = sum(h * w for h, w in spec.sizes) / len(spec.sizes)
+        times = []
+        for _ in range(max(1, args.steps)):
+            cb = batched_cpu_baseline(imgs, sub, budget_s=1e9)
+            times.append(cb)
+        v = sum(c["value"] for c in times) / len(times)
+        v = v * (sum(im.size // 3 for im in imgs) / len(imgs)) / mean_px
+        line = {"metric": "batched img/s", "value": v, "unit": "img/s", "n_gpus": args.gpus, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+                "config": batched_config(spec, [h * w for h, w in spec.sizes]),
+                "cpu_baseline": {"value": v, "unit": "img/s", "kind": "oracle", "cores": 1,
+                                 "sample": "%d size-stratified images of the batch per step, scaled to the batch's "
+                                           "mean image size" % len(imgs)},
+                "e2e": {"value": v, "unit": "img/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
     wl = synth.WORKLOADS[args.workload]
     img = wl.make(0)
     K = args.K
@@ -390,6 +677,10 @@ def main(argv=None) -> None:
     try:
         if args.impl == "reference":
             run_reference(args, rank, world)
+        elif args.workload == "batched":
+            run_batched(args, rank, world, local)
+        elif args.workload == "serving":
+            run_serving(args, rank, world, local)
         else:
             run_gpu(args, rank, world, local)
     finally:

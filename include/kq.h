@@ -200,6 +200,8 @@ typedef struct kq_batch_result {
     int32_t n_unique;     /* N' (also when above capacity) */
     kq_lloyd_stats lloyd; /* the final Lloyd run, as kq_lloyd writes it */
     int64_t sse_num;      /* sum over pixels of |pixel - palette[idx]|^2 (MSE numerator, Eq. 2) */
+    int64_t t_ns[5];      /* device clock (%globaltimer, ns) when the image's group started it and
+                             finished its histogram, seeding, Lloyd and mapping steps */
 } kq_batch_result;
 
 /* One image of a batch.  Host and device use the same layout: the array passed

@@ -37,7 +37,7 @@ constexpr size_t kHeaderBytes = 4096;       // queue counters at the start of th
 constexpr unsigned kBFull = 0xffffffffu;
 
 static_assert(sizeof(kq_batch_item) == 136, "kq_batch_item layout (LP64)");
-static_assert(sizeof(kq_batch_result) == 56 && offsetof(kq_batch_result, sse_num) == 48, "kq_batch_result layout");
+static_assert(sizeof(kq_batch_result) == 96 && offsetof(kq_batch_result, sse_num) == 48, "kq_batch_result layout");
 
 struct SlotMisc {
     unsigned long long ndc;
@@ -822,6 +822,8 @@ __device__ void run_item(Group &g, const kq_batch_item &it, BatchShared &bs, Llo
     }
     kq_batch_result *res = it.result;
     if (g.rank == 0 && tid == 0) {
+        res->t_ns[0] = (int64_t)globaltimer_ns();
+        for (int j = 1; j < 5; ++j) res->t_ns[j] = 0;
         res->status = KQ_OK;
         res->n_unique = 0;
         res->sse_num = 0;
@@ -843,10 +845,17 @@ __device__ void run_item(Group &g, const kq_batch_item &it, BatchShared &bs, Llo
         g();
         return;
     }
-    if (g.rank == 0 && tid == 0) res->n_unique = (int32_t)nu;
+    const bool lead = g.rank == 0 && tid == 0;
+    if (lead) {
+        res->n_unique = (int32_t)nu;
+        res->t_ns[1] = (int64_t)globaltimer_ns();
+    }
     group_seed(g, it, nu, bs, sh, dyn, &res->status);
+    if (lead) res->t_ns[2] = (int64_t)globaltimer_ns();
     group_lloyd(g, it, nu, it.K, it.eps, it.max_iter, it.palette, &res->lloyd, &res->status, sh, dyn);
+    if (lead) res->t_ns[3] = (int64_t)globaltimer_ns();
     group_map(g, it, nu, bs);
+    if (lead) res->t_ns[4] = (int64_t)globaltimer_ns();
 }
 
 __global__ void __launch_bounds__(kBT, 1) batch_kernel(BatchArgs a)

@@ -36,7 +36,7 @@ BATCH_ITEM_DTYPE = np.dtype([
     ("eps", "<f8"), ("lbg_eps", "<f8"), ("lbg_conv_eps", "<f8"), ("lbg_max_iter", "<i4"), ("K", "<i4"),
     ("scheme", "<i4"), ("max_iter", "<i4"), ("capacity", "<i4"), ("reserved", "<i4")], align=True)
 BATCH_RESULT_DTYPE = np.dtype([("status", "<i4"), ("n_unique", "<i4"), ("lloyd", STATS_DTYPE),
-                               ("sse_num", "<i8")], align=True)
+                               ("sse_num", "<i8"), ("t_ns", "<i8", (5,))], align=True)
 
 
 class BatchConfig(C.Structure):
@@ -406,11 +406,13 @@ class BatchQuantizer:
 
     def results(self) -> np.ndarray:
         """Every item's kq_batch_result (synchronizes)."""
-        out = np.zeros(self.n_items, dtype=BATCH_RESULT_DTYPE)
-        for i in range(self.n_items):
-            raw = self._view(i, "result").cpu().numpy().tobytes()
-            out[i] = np.frombuffer(raw, dtype=BATCH_RESULT_DTYPE)[0]
-        return out
+        if self.n_items == 0:
+            return np.zeros(0, dtype=BATCH_RESULT_DTYPE)
+        sz = BATCH_RESULT_DTYPE.itemsize
+        offs = torch.tensor([self.layout[i]["result"][0] for i in range(self.n_items)], dtype=torch.int64,
+                            device=self.arena.device)
+        raw = self.arena[offs[:, None] + torch.arange(sz, device=self.arena.device)[None, :]]
+        return np.frombuffer(raw.cpu().numpy().tobytes(), dtype=BATCH_RESULT_DTYPE).copy()
 
     def plan(self, cfg: BatchConfig) -> None:
         order, nb = kq_batch_plan(self.h_items, cfg)

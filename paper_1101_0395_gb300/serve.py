@@ -78,6 +78,9 @@ class Arena:
         self.free = merged
 
 
+RESULT_BYTES = 96  # sizeof(kq_batch_result)
+
+
 def request_layout(n_pixels: int, K: int, scratch_bytes) -> Tuple[Dict[str, Tuple[int, int]], int]:
     """Offsets (relative to a request's block) and sizes of its device buffers."""
     cap = max(0, min(int(n_pixels), 1 << 24))
@@ -85,7 +88,7 @@ def request_layout(n_pixels: int, K: int, scratch_bytes) -> Tuple[Dict[str, Tupl
     off = 0
     for name, size in (("rgb", 3 * n_pixels), ("idx", n_pixels), ("keys", 4 * cap), ("weights", 4 * cap),
                        ("labels", cap), ("scratch", scratch_bytes(cap)), ("centers", 24 * K),
-                       ("palette", 3 * K), ("result", 56)):
+                       ("palette", 3 * K), ("result", RESULT_BYTES)):
         lay[name] = (off, size)
         off = _align(off + max(size, 1))
     return lay, off
@@ -137,6 +140,7 @@ class Server:
         self.running: List[Wave] = []
         self.finished: List[Request] = []
         self.waves = 0
+        self.max_running = 0
 
     def now(self) -> float:
         return self.clock() - self.t0
@@ -183,6 +187,7 @@ class Server:
             handle = self.backend.launch(slot, batch)
             self.running.append(Wave(slot, batch, handle))
             self.waves += 1
+            self.max_running = max(self.max_running, len(self.running))
         return done
 
     def idle(self) -> bool:
@@ -335,3 +340,71 @@ class CudaBackend:
             r.palette = get("palette").reshape(-1, 3)
             r.centers = get("centers").view(np.float64).reshape(-1, 3)
             r.result = np.frombuffer(get("result").tobytes(), dtype=kq.BATCH_RESULT_DTYPE)[0]
+
+
+class PlainBackend:
+    """The plain per-image path behind the same scheduler, for comparison: each
+    request runs alone through the four single-image calls (kq.Quantizer) on
+    the whole GPU, one after another."""
+
+    def __init__(self, max_pixels: int, device=None):
+        import torch
+
+        from . import kq
+
+        self.torch, self.kq = torch, kq
+        self.device = torch.device("cuda") if device is None else torch.device(device)
+        self.max_pixels = int(max_pixels)
+
+    def scratch_bytes(self, cap: int) -> int:
+        return self.kq.kq_batch_scratch_bytes(cap)
+
+    def setup(self, pool_bytes: int, streams: int, max_wave: int) -> None:
+        torch, kq = self.torch, self.kq
+        self.q = [kq.Quantizer(self.max_pixels, device=self.device) for _ in range(streams)]
+        self.rgb = [torch.empty(3 * self.max_pixels, dtype=torch.uint8, device=self.device) for _ in range(streams)]
+        self.streams = [torch.cuda.Stream(device=self.device) for _ in range(streams)]
+        self.events = [torch.cuda.Event() for _ in range(streams)]
+        self.h_idx = [torch.empty(self.max_pixels, dtype=torch.uint8).pin_memory() for _ in range(streams)]
+        self.h_small = [torch.empty(4096, dtype=torch.uint8).pin_memory() for _ in range(streams)]
+
+    def launch(self, slot: int, batch: List[Request]):
+        torch = self.torch
+        s = self.streams[slot]
+        q = self.q[slot]
+        outs = []
+        with torch.cuda.stream(s):
+            for r in batch:
+                n = r.n_pixels
+                src = r.rgb if not isinstance(r.rgb, np.ndarray) else torch.from_numpy(np.ascontiguousarray(r.rgb))
+                d = self.rgb[slot][:3 * n]
+                d.copy_(src.reshape(-1), non_blocking=True)
+                res = q.quantize(d, r.K, r.scheme, r.seed, r.eps, r.max_iter, stream=s)
+                self.h_idx[slot][:n].copy_(res.idx, non_blocking=True)
+                hs = self.h_small[slot]
+                hs[:3 * r.K].copy_(res.palette.reshape(-1), non_blocking=True)
+                hs[1024:1024 + 24 * r.K].copy_(res.centers.reshape(-1).view(torch.uint8), non_blocking=True)
+                hs[3072:3112].copy_(res.stats[:40], non_blocking=True)
+                hs[3136:3144].copy_(res.sse_num.view(torch.uint8), non_blocking=True)
+                hs[3200:3204].copy_(res.n_unique.view(torch.uint8), non_blocking=True)
+                outs.append(n)
+            self.events[slot].record(s)
+        return (slot, self.events[slot], outs)
+
+    def done(self, handle) -> bool:
+        return handle[1].query()
+
+    def collect(self, handle, batch: List[Request]) -> None:
+        kq = self.kq
+        slot = handle[0]
+        hs = self.h_small[slot].numpy()
+        for r in batch:
+            r.idx = self.h_idx[slot][:r.n_pixels].numpy().copy()
+            r.palette = hs[:3 * r.K].copy().reshape(-1, 3)
+            r.centers = hs[1024:1024 + 24 * r.K].copy().view(np.float64).reshape(-1, 3)
+            res = np.zeros(1, dtype=kq.BATCH_RESULT_DTYPE)[0]
+            res["lloyd"] = np.frombuffer(hs[3072:3112].tobytes(), dtype=kq.STATS_DTYPE)[0]
+            res["sse_num"] = int(hs[3136:3144].view(np.int64)[0])
+            res["n_unique"] = int(hs[3200:3204].view(np.int32)[0])
+            res["status"] = res["lloyd"]["status"]
+            r.result = res

@@ -78,7 +78,8 @@ def _fake_items(spec):
 
 
 def test_batch_structs_and_scratch():
-    assert kq.BATCH_ITEM_DTYPE.itemsize == 136 and kq.BATCH_RESULT_DTYPE.itemsize == 56
+    assert kq.BATCH_ITEM_DTYPE.itemsize == 136 and kq.BATCH_RESULT_DTYPE.itemsize == 96
+    assert kq.BATCH_RESULT_DTYPE.itemsize == __import__('paper_1101_0395_gb300.serve', fromlist=['x']).RESULT_BYTES
     assert kq.kq_batch_scratch_bytes(1000) == 8192 + 16 * 32 + 256
     assert kq.kq_batch_scratch_bytes(0) == 256 and kq.kq_batch_scratch_bytes(-1) == 0
 

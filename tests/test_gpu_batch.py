@@ -143,7 +143,10 @@ def test_batch_graph_replay_is_repeatable(batch_inputs):
     for i, c in enumerate(CASES):
         if c[3] == "USER":
             continue
-        assert res0[i].tobytes() == res1[i].tobytes()
+        for f in ("status", "n_unique", "lloyd", "sse_num"):
+            assert res0[i][f].tobytes() == res1[i][f].tobytes(), (i, f)
+        t = res1[i]["t_ns"]
+        assert np.all(np.diff(t) >= 0) and t[0] > 0
         for name in ("idx", "keys", "weights", "labels", "centers", "palette"):
             off, size = bq.layout[i][name]
             assert torch.equal(outs[0][0][off:off + size], outs[1][0][off:off + size]), (i, name)

@@ -1,0 +1,56 @@
+"""Serving on the GPU: requests admitted by device memory and batched
+continuously give, request by request, exactly the result they give alone;
+mapping and histogram are checked against the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1101_0395_gb300 import kq, serve, synth
+from tests.gpu_helpers import require_cuda
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [(64, 64, 16, "KPP"), (300, 200, 128, "KPP"), (90, 120, 32, "MMX"), (256, 256, 256, "KPP"),
+         (40, 30, 8, "VAR"), (180, 240, 64, "DEN"), (128, 96, 200, "KPP"), (20, 20, 12, "FGY"),
+         (220, 160, 48, "SFF"), (140, 150, 100, "MMX")]
+
+
+def _requests():
+    out = []
+    for i, (h, w, K, s) in enumerate(SIZES):
+        img = synth.batch_image(h, w, 9100 + i)
+        out.append(serve.Request(rid=i, rgb=img.reshape(-1), K=K, scheme=s, seed=31 + i, arrival=0.0004 * i))
+    return out
+
+
+def _fields(r):
+    return (r.idx.tobytes(), r.palette.tobytes(), r.centers.tobytes(),
+            tuple(r.result[f].tobytes() for f in ("status", "n_unique", "lloyd", "sse_num")))
+
+
+def test_same_result_alone_and_in_the_mix():
+    require_cuda()
+    C = kq.kq_batch_max_cluster()
+    backend = serve.CudaBackend(cluster=min(C, 4), split_pixels=30000)
+    one = max(serve.request_layout(h * w, K, kq.kq_batch_scratch_bytes)[1] for h, w, K, _ in SIZES)
+    pool = 3 * one  # memory admits about three requests at a time
+    srv = serve.Server(backend, pool, streams=2, max_wave=3)
+    mix = _requests()
+    stats = serve.run_trace(srv, mix)
+    assert stats["requests"] == len(SIZES)
+    assert srv.arena.peak <= pool and srv.waves >= 4 and srv.max_running == 2
+    alone_srv = serve.Server(serve.CudaBackend(cluster=min(C, 4), split_pixels=30000), one, streams=1, max_wave=1)
+    for r in mix:
+        a = serve.Request(rid=r.rid, rgb=r.rgb, K=r.K, scheme=r.scheme, seed=r.seed)
+        alone_srv.submit(a)
+        alone_srv.drain()
+        assert a.result["status"] == kq.KQ_OK and r.result["status"] == kq.KQ_OK
+        assert _fields(a) == _fields(r), r.rid
+    # the served results themselves, against the oracle
+    for r in mix[:4]:
+        img = r.rgb.reshape(-1, 3)
+        keys, _ = oracle.histogram(img)
+        assert r.result["n_unique"] == keys.size
+        oidx, osse = oracle.map_pixels(img, r.palette)
+        assert np.array_equal(r.idx, oidx) and r.result["sse_num"] == osse
