@@ -210,8 +210,8 @@ typedef struct kq_batch_result {
 typedef struct kq_batch_item {
     const uint8_t *rgb;       /* n_pixels x 3 bytes, packed RGB8, any alignment */
     uint8_t *idx;             /* out: n_pixels palette indices */
-    uint32_t *keys;           /* out: capacity entries, unique colours ascending */
-    uint32_t *weights;        /* out: capacity entries, pixel counts */
+    uint32_t *keys;           /* out: capacity entries, unique colours ascending (16-byte aligned) */
+    uint32_t *weights;        /* out: capacity entries, pixel counts (16-byte aligned) */
     uint8_t *labels;          /* out: capacity entries, last assignment */
     void *scratch;            /* kq_batch_scratch_bytes(capacity) bytes, 256-byte aligned */
     double *centers;          /* K x 3; in for KQ_INIT_USER, out: final centres */

@@ -22,6 +22,7 @@ Parity status: every function above is pinned by ``tests/test_oracle_pins.py``
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes as C
 import math
 import os
@@ -33,7 +34,8 @@ from . import build as _build
 
 SCHEMES = {"FGY": 0, "LBG": 1, "MMX": 2, "DEN": 3, "VAR": 4, "SFF": 5, "KPP": 6}
 
-_lib: Optional[C.CDLL] = None
+_libs: Dict[str, C.CDLL] = {}
+_variant = "serial"
 
 _u8p = np.ctypeslib.ndpointer(dtype=np.uint8, flags="C_CONTIGUOUS")
 _u32p = np.ctypeslib.ndpointer(dtype=np.uint32, flags="C_CONTIGUOUS")
@@ -54,10 +56,25 @@ def _opt(ptr_type):
     return _Opt
 
 
+@contextlib.contextmanager
+def openmp():
+    """Within this block every call runs the OpenMP build of the same C source
+    (the assignment's colours split over the host cores).  For timing only: its
+    FP64 SSE sums depend on the thread count."""
+    global _variant
+    old = _variant
+    _variant = "openmp"
+    try:
+        yield
+    finally:
+        _variant = old
+
+
 def lib() -> C.CDLL:
-    global _lib
-    if _lib is None:
+    if _variant not in _libs:
         path = _build.build()
+        if _variant == "openmp":
+            path = _build.LIB_OMP
         L = C.CDLL(path)
         L.or_rand.restype = C.c_uint64
         L.or_rand.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32]
@@ -85,8 +102,8 @@ def lib() -> C.CDLL:
         L.or_var_channel.argtypes = [_u32p, _u32p, C.c_int64]
         L.or_den_quota.restype = None
         L.or_den_quota.argtypes = [_i64p, _i64p, C.c_int, _i64p]
-        _lib = L
-    return _lib
+        _libs[_variant] = L
+    return _libs[_variant]
 
 
 def _pixels(rgb: np.ndarray) -> np.ndarray:

@@ -110,6 +110,12 @@ OR_API double or_assign(const uint32_t *keys, const uint32_t *w, int64_t n, int 
                         uint8_t *labels, double *d1, double *d2)
 {
     double sse = 0.0;
+    /* The second build of this file (-fopenmp, used only to time the oracle on
+       all host cores) splits the colours over threads; the sum then depends on
+       the thread count, so the parity tests use the serial build. */
+#ifdef _OPENMP
+#pragma omp parallel for reduction(+ : sse) schedule(static)
+#endif
     for (int64_t i = 0; i < n; ++i) {
         int64_t r, g, b;
         key_rgb(keys[i], &r, &g, &b);

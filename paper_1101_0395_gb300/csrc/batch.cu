@@ -290,17 +290,46 @@ __device__ int64_t group_histogram(const Group &g, const kq_batch_item &it, Batc
 }
 
 // ---------------------------------------------------------------- k-means++ / minmax
-// Colour i belongs to 32-colour step i / 32; the steps are cut into contiguous
+// Colour i belongs to 128-colour step i / 128, lane l of a warp holding colours
+// 4l .. 4l + 3 of a step (16-byte loads).  The steps are cut into contiguous
 // ranges, one per warp of the group in (rank, warp) order, so the order of
-// (warp, step, lane) is the index order.  Per round each warp writes the running
-// sum of P = w (first round) or w D^2 at the end of each of its steps and its
-// total; the sample (the first colour whose running sum exceeds t) is then found
-// through the warp totals, the step sums and one step's lanes.
+// (warp, step, lane, element) is the index order.  Per round each warp writes the
+// running sum of P = w (first round) or w D^2 at the end of each of its steps and
+// its total; the sample (the first colour whose running sum exceeds t) is then
+// found through the warp totals, the step sums, one step's lane sums and one
+// lane's four colours.
+constexpr int kStep = 128;
+
 struct FarScratch {
-    uint32_t *d2;              // [2][cap]
-    unsigned long long *sp;    // [2][steps]
-    int64_t cap, steps;        // buffer strides: capacity and ceil(capacity / 32)
+    uint32_t *d2;              // [2][cap4]
+    unsigned long long *sp;    // [2][sstride]
+    int64_t cap4, sstride;     // buffer strides
 };
+
+__host__ __device__ __forceinline__ int64_t far_cap4(int64_t cap) { return (cap + 3) / 4 * 4; }
+__host__ __device__ __forceinline__ int64_t far_sstride(int64_t cap) { return (cap + kStep - 1) / kStep + 1; }
+
+// Four consecutive 32-bit values from i (16-byte aligned), zero past n.
+__device__ __forceinline__ uint4 ld4(const uint32_t *p, int64_t i, int64_t n)
+{
+    if (i + 3 < n) return __ldcg(reinterpret_cast<const uint4 *>(p + i));
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (i < n) v.x = __ldcg(p + i);
+    if (i + 1 < n) v.y = __ldcg(p + i + 1);
+    if (i + 2 < n) v.z = __ldcg(p + i + 2);
+    return v;
+}
+
+__device__ __forceinline__ void st4(uint32_t *p, int64_t i, int64_t n, uint4 v)
+{
+    if (i + 3 < n) {
+        *reinterpret_cast<uint4 *>(p + i) = v;
+        return;
+    }
+    if (i < n) p[i] = v.x;
+    if (i + 1 < n) p[i + 1] = v.y;
+    if (i + 2 < n) p[i + 2] = v.z;
+}
 
 __device__ uint32_t far_locate(const kq_batch_item &it, const FarScratch &fs, int64_t n, int GW, int buf, int r,
                                const unsigned long long *wt)
@@ -336,9 +365,9 @@ __device__ uint32_t far_locate(const kq_batch_item &it, const FarScratch &fs, in
         run += __shfl_sync(kBFull, x, 31);
     }
     // the step of warp gstar holding the sample: blocks of 32 steps, then the step
-    const unsigned long long *sp = fs.sp + (size_t)buf * fs.steps;
+    const unsigned long long *sp = fs.sp + (size_t)buf * fs.sstride;
     int64_t slo, shi;
-    slice_of((n + 31) / 32, gstar, GW, &slo, &shi);  // the partition group_far used
+    slice_of((n + kStep - 1) / kStep, gstar, GW, &slo, &shi);  // the partition group_far used
     int64_t sstar = shi - 1;
     unsigned long long before = 0ull;  // running sum of the warp before step sstar
     for (int64_t sb = slo; sb < shi; sb += 1024) {
@@ -364,20 +393,35 @@ __device__ uint32_t far_locate(const kq_batch_item &it, const FarScratch &fs, in
     }
     const unsigned long long resid2 = resid - before;
     if (sstar < 0) sstar = 0;  // only for an all-zero total, which valid inputs never give
-    const int64_t i = sstar * 32 + lane;
-    unsigned long long p = 0ull;
-    if (i < n) {
-        const unsigned long long wi = __ldcg(it.weights + i);
-        p = r == 0 ? wi : wi * (unsigned long long)__ldcg(fs.d2 + (size_t)buf * fs.cap + i);
+    // the lane, then the colour, within step sstar
+    const int64_t i0 = sstar * kStep + 4 * lane;
+    const uint4 w4 = ld4(it.weights, i0, n);
+    unsigned long long p[4] = {w4.x, w4.y, w4.z, w4.w};
+    if (r > 0) {
+        const uint4 d4 = ld4(fs.d2 + (size_t)buf * fs.cap4, i0, n);
+        p[0] *= d4.x;
+        p[1] *= d4.y;
+        p[2] *= d4.z;
+        p[3] *= d4.w;
     }
-    unsigned long long x = p;
+    const unsigned long long ps = p[0] + p[1] + p[2] + p[3];
+    unsigned long long x = ps;
     for (int o = 1; o < 32; o <<= 1) {
         const unsigned long long y = __shfl_up_sync(kBFull, x, o);
         if (lane >= o) x += y;
     }
-    const unsigned bal = __ballot_sync(kBFull, i < n && x > resid2);
+    const unsigned bal = __ballot_sync(kBFull, x > resid2);
     const int l = bal ? __ffs(bal) - 1 : 0;
-    const int64_t istar = sstar * 32 + l;
+    unsigned long long acc = __shfl_sync(kBFull, x - ps, l);  // running sum before lane l
+    int64_t istar = sstar * kStep + 4 * l + 3;
+    for (int j = 0; j < 4; ++j) {
+        const unsigned long long pj = __shfl_sync(kBFull, p[j], l);
+        if (acc + pj > resid2) {
+            istar = sstar * kStep + 4 * l + j;
+            break;
+        }
+        acc += pj;
+    }
     return __ldcg(it.keys + (istar < n ? istar : n - 1));
 }
 
@@ -388,54 +432,64 @@ __device__ void group_far(const Group &g, const kq_batch_item &it, int64_t n, in
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int GW = g.C * kBW, gw = g.rank * kBW + warp;
     FarScratch fs;
-    fs.cap = it.capacity;
-    fs.steps = (fs.cap + 31) / 32;
+    fs.cap4 = far_cap4(it.capacity);
+    fs.sstride = far_sstride(it.capacity);
     fs.d2 = reinterpret_cast<uint32_t *>(it.scratch);
     fs.sp = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(it.scratch) +
-                                                   align_up(sizeof(uint32_t) * 2 * (size_t)fs.cap, 256));
-    const int64_t steps = (n + 31) / 32;
+                                                   align_up(sizeof(uint32_t) * 2 * (size_t)fs.cap4, 256));
+    const int64_t steps = (n + kStep - 1) / kStep;
     int64_t slo, shi;
     slice_of(steps, gw, GW, &slo, &shi);
     SlotMisc *ms = g.misc();
     const uint32_t *__restrict__ keys = it.keys;
     const uint32_t *__restrict__ wts = it.weights;
     uint32_t ckey = 0u;
+    constexpr int U = 4;  // steps in flight per warp
     for (int r = 0; r < K; ++r) {
         const int buf = r & 1;
         if (mode == 1 && r == 0) {
             ckey = __ldcg(keys + below(rand64(it.seed, 3, 0), (uint64_t)n));
         } else {
-            uint32_t *__restrict__ d2w = fs.d2 + (size_t)buf * fs.cap;
-            const uint32_t *__restrict__ d2r = fs.d2 + (size_t)(buf ^ 1) * fs.cap;
-            unsigned long long *__restrict__ sp = fs.sp + (size_t)buf * fs.steps;
+            uint32_t *__restrict__ d2w = fs.d2 + (size_t)buf * fs.cap4;
+            const uint32_t *__restrict__ d2r = fs.d2 + (size_t)(buf ^ 1) * fs.cap4;
+            unsigned long long *__restrict__ sp = fs.sp + (size_t)buf * fs.sstride;
             unsigned long long run = 0ull, best = 0ull;
-            for (int64_t s0 = slo; s0 < shi; s0 += 4) {
-                uint32_t key[4], wv[4], dp[4];
+            for (int64_t s0 = slo; s0 < shi; s0 += U) {
+                uint4 k4[U], w4[U], d4[U];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int64_t i = (s0 + q) * 32 + lane;
-                    const bool ok = s0 + q < shi && i < n;
-                    key[q] = ok ? __ldcg(keys + i) : 0u;
-                    wv[q] = ok ? __ldcg(wts + i) : 0u;
-                    dp[q] = (ok && r > 1) ? __ldcg(d2r + i) : 0xFFFFFFFFu;
+                for (int q = 0; q < U; ++q) {
+                    const int64_t i = (s0 + q) * kStep + 4 * lane;
+                    const int64_t lim = s0 + q < shi ? n : 0;
+                    k4[q] = ld4(keys, i, lim);
+                    w4[q] = mode == 0 ? ld4(wts, i, lim) : make_uint4(0u, 0u, 0u, 0u);
+                    d4[q] = r > 1 ? ld4(d2r, i, lim) : make_uint4(~0u, ~0u, ~0u, ~0u);
                 }
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
+                for (int q = 0; q < U; ++q) {
                     if (s0 + q >= shi) break;
-                    const int64_t i = (s0 + q) * 32 + lane;
-                    const bool ok = i < n;
+                    const int64_t i = (s0 + q) * kStep + 4 * lane;
                     unsigned long long p = 0ull;
-                    if (ok) {
-                        if (r == 0) {
-                            p = wv[q];
+                    if (r == 0) {
+                        p = (unsigned long long)w4[q].x + w4[q].y + w4[q].z + w4[q].w;
+                    } else {
+                        uint4 md;
+                        md.x = min(d4[q].x, key_dist2(k4[q].x, ckey));
+                        md.y = min(d4[q].y, key_dist2(k4[q].y, ckey));
+                        md.z = min(d4[q].z, key_dist2(k4[q].z, ckey));
+                        md.w = min(d4[q].w, key_dist2(k4[q].w, ckey));
+                        st4(d2w, i, n, md);
+                        if (mode == 0) {
+                            p = (unsigned long long)w4[q].x * md.x + (unsigned long long)w4[q].y * md.y +
+                                (unsigned long long)w4[q].z * md.z + (unsigned long long)w4[q].w * md.w;
                         } else {
-                            const uint32_t md = min(dp[q], key_dist2(key[q], ckey));
-                            d2w[i] = md;
-                            if (mode == 0) {
-                                p = (unsigned long long)wv[q] * md;
-                            } else {
-                                const unsigned long long pk = mmx_pack(md, key[q]);
-                                best = pk > best ? pk : best;
+                            const uint32_t mm[4] = {md.x, md.y, md.z, md.w};
+                            const uint32_t kk[4] = {k4[q].x, k4[q].y, k4[q].z, k4[q].w};
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                if (i + j < n) {
+                                    const unsigned long long pk = mmx_pack(mm[j], kk[j]);
+                                    best = pk > best ? pk : best;
+                                }
                             }
                         }
                     }
@@ -805,9 +859,15 @@ __device__ void group_map(const Group &g, const kq_batch_item &it, int64_t nu, B
 }
 
 // ---------------------------------------------------------------- one image
+__host__ __device__ __forceinline__ bool item_aligned(const kq_batch_item &it)
+{
+    return ((reinterpret_cast<uintptr_t>(it.keys) | reinterpret_cast<uintptr_t>(it.weights)) & 15u) == 0 &&
+           (reinterpret_cast<uintptr_t>(it.scratch) & 255u) == 0;
+}
+
 __device__ __forceinline__ bool item_ok(const kq_batch_item &it)
 {
-    return it.n_pixels >= 0 && (it.rgb || it.n_pixels == 0) && (it.idx || it.n_pixels == 0) && it.K >= 1 &&
+    return item_aligned(it) && it.n_pixels >= 0 && (it.rgb || it.n_pixels == 0) && (it.idx || it.n_pixels == 0) && it.K >= 1 &&
            it.K <= kMaxK && it.scheme >= KQ_INIT_FGY && it.scheme <= KQ_INIT_USER && it.max_iter >= 1 &&
            it.capacity >= 0 && it.keys && it.weights && it.labels && it.scratch && it.centers && it.palette &&
            it.result && (it.scheme != KQ_INIT_LBG || it.lbg_max_iter >= 1);
@@ -954,7 +1014,7 @@ int grid_for(const BatchDev &d, int C) { return C > 1 ? d.clusters[C] * C : d.cl
 
 bool host_item_ok(const kq_batch_item &it)
 {
-    return it.n_pixels >= 0 && (it.rgb || it.n_pixels == 0) && (it.idx || it.n_pixels == 0) && it.K >= 1 &&
+    return item_aligned(it) && it.n_pixels >= 0 && (it.rgb || it.n_pixels == 0) && (it.idx || it.n_pixels == 0) && it.K >= 1 &&
            it.K <= kMaxK && it.scheme >= KQ_INIT_FGY && it.scheme <= KQ_INIT_USER && it.max_iter >= 1 &&
            it.capacity >= 0 && it.keys && it.weights && it.labels && it.scratch && it.centers && it.palette &&
            it.result && it.eps == it.eps && (it.scheme != KQ_INIT_LBG || it.lbg_max_iter >= 1);
@@ -968,8 +1028,8 @@ using namespace kq;
 extern "C" KQ_API size_t kq_batch_scratch_bytes(int32_t capacity)
 {
     if (capacity < 0) return 0;
-    const size_t cap = (size_t)capacity;
-    return align_up(sizeof(uint32_t) * 2 * cap, 256) + sizeof(unsigned long long) * 2 * ((cap + 31) / 32) + 256;
+    return align_up(sizeof(uint32_t) * 2 * (size_t)far_cap4(capacity), 256) +
+           sizeof(unsigned long long) * 2 * (size_t)far_sstride(capacity) + 256;
 }
 
 extern "C" KQ_API size_t kq_batch_workspace_size(void)

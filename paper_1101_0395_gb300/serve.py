@@ -366,7 +366,7 @@ class PlainBackend:
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(streams)]
         self.events = [torch.cuda.Event() for _ in range(streams)]
         self.h_idx = [torch.empty(self.max_pixels, dtype=torch.uint8).pin_memory() for _ in range(streams)]
-        self.h_small = [torch.empty(4096, dtype=torch.uint8).pin_memory() for _ in range(streams)]
+        self.h_small = [torch.empty(8192, dtype=torch.uint8).pin_memory() for _ in range(streams)]
 
     def launch(self, slot: int, batch: List[Request]):
         torch = self.torch
@@ -384,9 +384,9 @@ class PlainBackend:
                 hs = self.h_small[slot]
                 hs[:3 * r.K].copy_(res.palette.reshape(-1), non_blocking=True)
                 hs[1024:1024 + 24 * r.K].copy_(res.centers.reshape(-1).view(torch.uint8), non_blocking=True)
-                hs[3072:3112].copy_(res.stats[:40], non_blocking=True)
-                hs[3136:3144].copy_(res.sse_num.view(torch.uint8), non_blocking=True)
-                hs[3200:3204].copy_(res.n_unique.view(torch.uint8), non_blocking=True)
+                hs[7168:7208].copy_(res.stats[:40], non_blocking=True)
+                hs[7232:7240].copy_(res.sse_num.view(torch.uint8), non_blocking=True)
+                hs[7296:7300].copy_(res.n_unique.view(torch.uint8), non_blocking=True)
                 outs.append(n)
             self.events[slot].record(s)
         return (slot, self.events[slot], outs)
@@ -403,8 +403,8 @@ class PlainBackend:
             r.palette = hs[:3 * r.K].copy().reshape(-1, 3)
             r.centers = hs[1024:1024 + 24 * r.K].copy().view(np.float64).reshape(-1, 3)
             res = np.zeros(1, dtype=kq.BATCH_RESULT_DTYPE)[0]
-            res["lloyd"] = np.frombuffer(hs[3072:3112].tobytes(), dtype=kq.STATS_DTYPE)[0]
-            res["sse_num"] = int(hs[3136:3144].view(np.int64)[0])
-            res["n_unique"] = int(hs[3200:3204].view(np.int32)[0])
+            res["lloyd"] = np.frombuffer(hs[7168:7208].tobytes(), dtype=kq.STATS_DTYPE)[0]
+            res["sse_num"] = int(hs[7232:7240].view(np.int64)[0])
+            res["n_unique"] = int(hs[7296:7300].view(np.int32)[0])
             res["status"] = res["lloyd"]["status"]
             r.result = res

@@ -70,7 +70,7 @@ def _fake_items(spec):
     items = np.zeros(len(spec), dtype=kq.BATCH_ITEM_DTYPE)
     for i, (n, K) in enumerate(spec):
         for f in ("rgb", "idx", "keys", "weights", "labels", "scratch", "centers", "palette", "result"):
-            items[i][f] = (1 << 20) + 4096 * i  # never dereferenced by the planner
+            items[i][f] = (1 << 20) + 4096 * i  # aligned; never dereferenced by the planner
         items[i]["n_pixels"], items[i]["K"], items[i]["scheme"] = n, K, 6
         items[i]["max_iter"], items[i]["capacity"], items[i]["eps"] = 100, n, 1e-4
         items[i]["lbg_max_iter"] = 100
@@ -80,8 +80,8 @@ def _fake_items(spec):
 def test_batch_structs_and_scratch():
     assert kq.BATCH_ITEM_DTYPE.itemsize == 136 and kq.BATCH_RESULT_DTYPE.itemsize == 96
     assert kq.BATCH_RESULT_DTYPE.itemsize == __import__('paper_1101_0395_gb300.serve', fromlist=['x']).RESULT_BYTES
-    assert kq.kq_batch_scratch_bytes(1000) == 8192 + 16 * 32 + 256
-    assert kq.kq_batch_scratch_bytes(0) == 256 and kq.kq_batch_scratch_bytes(-1) == 0
+    assert kq.kq_batch_scratch_bytes(1000) == 8192 + 16 * 9 + 256
+    assert kq.kq_batch_scratch_bytes(0) == 272 and kq.kq_batch_scratch_bytes(-1) == 0
 
 
 def test_batch_planner_orders_largest_work_first():
@@ -93,7 +93,7 @@ def test_batch_planner_orders_largest_work_first():
     order, nb = kq.kq_batch_plan(items, kq.BatchConfig(4, 0, 6000))
     assert nb == 1 and list(order) == [3, 1, 0, 2]
     for field, value in (("K", 0), ("K", 257), ("scheme", 8), ("max_iter", 0), ("n_pixels", -1),
-                         ("capacity", -1), ("keys", 0)):
+                         ("capacity", -1), ("keys", 0), ("keys", (1 << 20) + 8), ("scratch", (1 << 20) + 16)):
         bad = items.copy()
         bad[1][field] = value
         with pytest.raises(kq.KqError):
