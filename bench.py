@@ -10,6 +10,7 @@ timed).  Prints one JSON line (rank 0).
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
   python bench.py --workload batched [--count 512]     # img/s, one launch per batch
   python bench.py --workload serving [--rate 200]      # p50/p99 latency under Poisson arrivals
+  python bench.py --workload table1                    # k-means on all pixels vs WSM (Table 1, Fig. 2)
 
 Under torchrun (N > 1) every rank quantizes its own image (independent
 replicas, no data exchange); value = pixels of all ranks / max step time.
@@ -432,7 +433,8 @@ def run_serving(args, rank, world, local) -> None:
     pool_bytes = 48 << 30
     props = torch.cuda.get_device_properties(dev)
     clocks = ClockSampler("GPU-%s" % props.uuid if getattr(props, "uuid", None) else str(local))
-    srv = serve.Server(serve.CudaBackend(cluster, split, device=dev), pool_bytes, streams=2, max_wave=64)
+    srv = serve.Server(serve.CudaBackend(cluster, split, device=dev, solo_max_pixels=max_px), pool_bytes, streams=2,
+                       max_wave=64)
     srv.drain()
     for r in requests(8):
         srv.submit(r)
@@ -444,6 +446,7 @@ def run_serving(args, rank, world, local) -> None:
     out = serve.run_trace(srv, reqs)
     clk = clocks.stop()
     h2d, d2h = srv.backend.h2d_bytes - h2d0, srv.backend.d2h_bytes - d2h0
+    waves, solo_waves = srv.waves, srv.backend.solo_waves
     del srv
     torch.cuda.empty_cache()
     # the plain per-image path behind the same scheduler, on the same trace
@@ -456,7 +459,8 @@ def run_serving(args, rank, world, local) -> None:
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "serving: Poisson arrivals at %g req/s for %g s; image side log-uniform 256-4096 "
                                    "(aspect 0.5-2, pool of 48 images), K uniform 8..256, %s seeds, eps=1e-4, "
-                                   "<=100 passes; memory-admitted continuous batching on 2 streams"
+                                   "<=100 passes; memory-admitted continuous batching on 2 streams (a lone request on an idle "
+                                   "device runs on the whole GPU)"
                                    % (args.rate, args.duration, SCHEME),
                        "requests": len(reqs), "launch_shape": {"cluster": cluster, "split_pixels": split},
                        "pool_bytes": pool_bytes, "l2": "inputs larger than L2 (no flush)"},
@@ -465,8 +469,115 @@ def run_serving(args, rank, world, local) -> None:
                     "d2h_bytes_per_step": int(d2h / max(1, len(reqs)))},
             "gpu_launches": None,
             "p50_ms": out["p50_ms"], "img_per_s": out["img_per_s"], "mpix_per_s": out["mpix_per_s"],
+            "waves": waves, "solo_waves": solo_waves,
             "per_image_path": {"p50_ms": pout["p50_ms"], "p99_ms": pout["p99_ms"], "img_per_s": pout["img_per_s"],
                                "same_sse_requests": same}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_table1(args, rank, world, local) -> None:
+    """The Table 1 analogue (Section 3.2): k-means on all N pixels against Weighted
+    Sort-Means on the unique colours, both from the same Forgy centres for 20 fixed
+    passes; the NDC per pixel per pass and the GPU times (palette + mapping), then a
+    Fig. 2-style sweep of the WSM time over K."""
+    import numpy as np
+    import torch
+
+    from paper_1101_0395_gb300 import kq, synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = synth.WORKLOADS["paper_512"]
+    img = wl.make(rank)
+    n = img.size // 3
+    rgb = torch.from_numpy(img.reshape(-1)).to(dev)
+    q = kq.Quantizer(n, device=dev)
+    pk = torch.zeros(n, dtype=torch.int32, device=dev)
+    pw = torch.zeros(n, dtype=torch.int32, device=dev)
+    pn = torch.zeros(1, dtype=torch.int32, device=dev)
+    ws2 = torch.zeros(kq.kq_workspace_size(n, 256), dtype=torch.uint8, device=dev)
+    lab2 = torch.zeros(n, dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    idx = q.idx[:n]
+
+    def timed(fn, reps=5):
+        ts = []
+        for r in range(reps + 2):
+            flush.fill_(r & 255)
+            a, b = torch.cuda.Event(True), torch.cuda.Event(True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            if r >= 2:
+                ts.append(a.elapsed_time(b))
+        return float(np.median(ts))
+
+    rows = []
+    sweep = {}
+    for K in (2, 4, 8, 16, 32, 64, 128, 256):
+        kq.kq_histogram(rgb, q.keys, q.weights, q.n_unique, q.ws)
+        c0 = torch.zeros(3 * K, dtype=torch.float64, device=dev)
+        kq.kq_seed(q.keys, q.weights, q.n_unique, K, "FGY", SEED, c0, q.ws)
+        c_w, c_k = c0.clone(), c0.clone()
+        pal_w = torch.zeros(3 * K, dtype=torch.uint8, device=dev)
+        pal_k = torch.zeros(3 * K, dtype=torch.uint8, device=dev)
+
+        def wsm():
+            kq.kq_histogram(rgb, q.keys, q.weights, q.n_unique, q.ws)
+            c_w.copy_(c0)
+            kq.kq_lloyd(q.keys, q.weights, q.n_unique, K, c_w, -1.0, 20, q.labels, pal_w, q.ws, stats=q.stats)
+            kq.kq_map(rgb, q.keys, q.weights, q.n_unique, pal_w, K, idx, q.ws, sse_num=q.sse_num)
+
+        def km():
+            kq.kq_pixel_keys(rgb, pk, pw, pn)
+            c_k.copy_(c0)
+            kq.kq_lloyd(pk, pw, pn, K, c_k, -1.0, 20, lab2, pal_k, ws2, stats=q.stats, flags=kq.LLOYD_DENSE)
+            kq.kq_map(rgb, q.keys, q.weights, q.n_unique, pal_k, K, idx, q.ws, sse_num=q.sse_num)
+
+        t_w = timed(wsm)
+        st_w = kq.parse_stats(q.stats)
+        nu = int(q.n_unique.item())
+        sweep[str(K)] = t_w
+        if K >= 32:
+            t_k = timed(km, reps=3)
+            st_k = kq.parse_stats(q.stats)
+            same = bool(torch.equal(c_w, c_k) and torch.equal(pal_w, pal_k))
+            rows.append({"K": K, "ndc_wsm_per_pixel_per_pass": st_w["ndc"] / (n * 20.0),
+                         "ndc_wsm_per_colour_per_pass": st_w["ndc"] / (nu * 20.0), "ndc_km": st_k["ndc"] / (n * 20.0),
+                         "ms_wsm": t_w, "ms_km": t_k, "speedup": t_k / t_w, "same_centres": same})
+    # 2:1 subsampling before the unique-colour sampling (Section 2.2): palette from
+    # the pixels with even x and y, every pixel mapped; time and MSE beside the full run
+    sub = []
+    h, w = wl.height, wl.width
+    for K in (64, 256):
+        c = torch.zeros(3 * K, dtype=torch.float64, device=dev)
+        pal = torch.zeros(3 * K, dtype=torch.uint8, device=dev)
+        out = {}
+        for stride in (1, 2):
+            def run():
+                kq.kq_histogram_strided(rgb, h, w, stride, q.keys, q.weights, q.n_unique, q.ws)
+                kq.kq_seed(q.keys, q.weights, q.n_unique, K, SCHEME, SEED, c, q.ws)
+                kq.kq_lloyd(q.keys, q.weights, q.n_unique, K, c, wl.eps, wl.max_iter, q.labels, pal, q.ws,
+                            stats=q.stats)
+                if stride != 1:
+                    kq.kq_histogram(rgb, q.keys, q.weights, q.n_unique, q.ws)
+                kq.kq_map(rgb, q.keys, q.weights, q.n_unique, pal, K, idx, q.ws, sse_num=q.sse_num)
+
+            t = timed(run)
+            out[stride] = {"ms": t, "mse": int(q.sse_num.item()) / n, "iters": kq.parse_stats(q.stats)["iters"]}
+        sub.append({"K": K, "full": out[1], "sub2": out[2], "mse_ratio": out[2]["mse"] / out[1]["mse"],
+                    "speedup": out[1]["ms"] / out[2]["ms"]})
+    sp = [r["speedup"] for r in rows]
+    line = {"metric": "Table 1 analogue: k-means / WSM time, 20 passes from the same Forgy centres",
+            "value": float(np.mean(sp)), "unit": "x", "n_gpus": world, "steps": 5, "warmup": 2,
+            "ms_per_step": rows[-1]["ms_wsm"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "paper_512 image 0 (%dx%d, N'=%d), Forgy seeds, 20 fixed passes, times include "
+                                   "the histogram (WSM) and the mapping (both)" % (wl.height, wl.width, nu),
+                       "l2": "flushed between runs"},
+            "rows": rows, "wsm_ms_by_K": sweep, "subsampling_2to1": sub, "gpu_launches": None}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -697,6 +808,8 @@ def main(argv=None) -> None:
             run_batched(args, rank, world, local)
         elif args.workload == "serving":
             run_serving(args, rank, world, local)
+        elif args.workload == "table1":
+            run_table1(args, rank, world, local)
         else:
             run_gpu(args, rank, world, local)
     finally:

@@ -122,6 +122,20 @@ KQ_API int kq_histogram(const uint8_t *rgb, int64_t n_pixels, uint32_t *keys, ui
                  int32_t *n_unique, void *ws, size_t ws_bytes, kq_stream_t stream);
 
 /*
+ * kq_histogram over a deterministic subsample: only the pixels (x, y) with x and y
+ * multiples of `stride`.  stride = 2 is the 2:1 subsampling in both directions of
+ * Section 2.2 (data sampling), combined there with the unique-colour sampling;
+ * stride = 1 is the whole image.
+ *   rgb        height rows of width x 3 bytes; row y starts at rgb + y * pitch.
+ *   pitch      bytes between rows, >= 3 * width.
+ * Other arguments and results as kq_histogram.  Note that kq_map needs the
+ * histogram of every pixel it maps (kq_histogram of the whole image).
+ */
+KQ_API int kq_histogram_strided(const uint8_t *rgb, int32_t height, int32_t width, int64_t pitch, int32_t stride,
+                                uint32_t *keys, uint32_t *weights, int32_t capacity, int32_t *n_unique, void *ws,
+                                size_t ws_bytes, kq_stream_t stream);
+
+/*
  * Initial centres by a generic scheme of Section 2.3.
  *   keys, weights, n_unique   the output of kq_histogram.
  *   K          palette size, 1..256.  When K >= N' the centres are the N'
@@ -302,6 +316,18 @@ KQ_API int kq_batch_tune(const kq_batch_item *h_items, const kq_batch_item *item
 KQ_API int kq_lloyd_noalloc(const uint32_t *keys, const uint32_t *weights, const int32_t *n_unique, int32_t K,
                             double *centers, double eps, int32_t max_iter, uint32_t flags, uint8_t *labels,
                             uint8_t *palette, kq_lloyd_stats *stats, double *sse_hist, kq_stream_t stream);
+
+/*
+ * The plain k-means baseline of Table 1 (Section 3.2): every pixel as its own
+ * point.  Writes keys[i] = (R << 16) | (G << 8) | B of pixel i (in pixel order,
+ * not unique), weights[i] = 1 when `weights` is not NULL, and *n_out = n_pixels
+ * when `n_out` is not NULL, so that kq_lloyd run on (keys, weights, n_out) with
+ * KQ_LLOYD_DENSE is k-means on all N pixels.  Not a step of Weighted Sort-Means.
+ *   rgb        n_pixels x 3 bytes.   keys, weights   n_pixels entries (device).
+ * Returns KQ_EINVAL for n_pixels outside 0 .. 2^31 - 1 or a missing buffer.
+ */
+KQ_API int kq_pixel_keys(const uint8_t *rgb, int64_t n_pixels, uint32_t *keys, uint32_t *weights, int32_t *n_out,
+                         kq_stream_t stream);
 
 /* Device status word of `ws` copied to *h_status (synchronizes `stream`). */
 KQ_API int kq_status_read(const void *ws, int32_t *h_status, kq_stream_t stream);

@@ -95,6 +95,20 @@ int kq_histogram(const uint8_t *rgb, int64_t n_pixels, uint32_t *keys, uint32_t 
     return kq::launch_histogram(rgb, n_pixels, keys, weights, capacity, n_unique, ws, L, (cudaStream_t)stream);
 }
 
+int kq_histogram_strided(const uint8_t *rgb, int32_t height, int32_t width, int64_t pitch, int32_t stride,
+                         uint32_t *keys, uint32_t *weights, int32_t capacity, int32_t *n_unique, void *ws,
+                         size_t ws_bytes, kq_stream_t stream)
+{
+    Layout L;
+    if (!ws_ok(ws, ws_bytes, &L)) return KQ_EINVAL;
+    if (height < 0 || width < 0 || stride < 1 || capacity < 0 || !n_unique) return KQ_EINVAL;
+    if (pitch < 3 * (int64_t)width) return KQ_EINVAL;
+    if ((int64_t)height * width > 0 && !rgb) return KQ_EINVAL;
+    if (capacity > 0 && (!keys || !weights)) return KQ_EINVAL;
+    return kq::launch_histogram_strided(rgb, height, width, pitch, stride, keys, weights, capacity, n_unique, ws, L,
+                                        (cudaStream_t)stream);
+}
+
 int kq_seed(const uint32_t *keys, const uint32_t *weights, const int32_t *n_unique, int32_t K, int32_t scheme,
             uint64_t seed, const kq_seed_params *params, double *centers, void *ws, size_t ws_bytes,
             kq_stream_t stream)
@@ -137,6 +151,15 @@ int kq_map(const uint8_t *rgb, int64_t n_pixels, const uint32_t *keys, const uin
     if (K < 1 || K > kq::kMaxK) return KQ_EINVAL;
     return kq::launch_map(rgb, n_pixels, keys, weights, n_unique, palette, K, idx, sse_num, ws, L,
                           (cudaStream_t)stream);
+}
+
+int kq_pixel_keys(const uint8_t *rgb, int64_t n_pixels, uint32_t *keys, uint32_t *weights, int32_t *n_out,
+                  kq_stream_t stream)
+{
+    if (n_pixels < 0 || n_pixels > 0x7FFFFFFF) return KQ_EINVAL;
+    if (n_pixels > 0 && (!rgb || !keys)) return KQ_EINVAL;
+    if (n_pixels == 0 && !n_out) return KQ_OK;
+    return kq::launch_pixel_keys(rgb, n_pixels, keys, weights, n_out, (cudaStream_t)stream);
 }
 
 int kq_status_read(const void *ws, int32_t *h_status, kq_stream_t stream)

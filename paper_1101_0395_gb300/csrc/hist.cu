@@ -190,7 +190,70 @@ __global__ void __launch_bounds__(kEmitBlock) hist_emit(uint32_t *__restrict__ b
     }
 }
 
+// hist_count over the pixels (x, y) with x and y multiples of `stride` of an
+// H x W image whose rows start `pitch` bytes apart (the 2:1 subsampling of
+// Section 2.2 for stride 2).
+__global__ void __launch_bounds__(kCountBlock) hist_count_strided(const uint8_t *__restrict__ rgb, int32_t h,
+                                                                  int32_t w, int64_t pitch, int32_t stride,
+                                                                  uint32_t *__restrict__ cnt,
+                                                                  uint32_t *__restrict__ bits)
+{
+    const int64_t hs = (h + stride - 1) / stride, ws = (w + stride - 1) / stride;
+    const int64_t total = hs * ws;
+    const int64_t nth = (int64_t)gridDim.x * kCountBlock;
+    for (int64_t q = (int64_t)blockIdx.x * kCountBlock + threadIdx.x; q < total; q += nth) {
+        const int64_t y = (q / ws) * stride, x = (q % ws) * stride;
+        const uint8_t *px = rgb + y * pitch + 3 * x;
+        add_colour(cnt, bits, ((uint32_t)px[0] << 16) | ((uint32_t)px[1] << 8) | (uint32_t)px[2]);
+    }
+}
+
+// Every pixel as its own point of weight 1 (the k-means baseline of Table 1).
+__global__ void __launch_bounds__(256) pixel_keys(const uint8_t *__restrict__ rgb, int64_t n,
+                                                  uint32_t *__restrict__ keys, uint32_t *__restrict__ w,
+                                                  int32_t *__restrict__ n_out)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
+        keys[p] = key_at(rgb, p);
+        if (w) w[p] = 1u;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && n_out) *n_out = (int32_t)n;
+}
+
 }  // namespace
+
+int launch_pixel_keys(const uint8_t *rgb, int64_t n, uint32_t *keys, uint32_t *weights, int32_t *n_out,
+                      cudaStream_t s)
+{
+    const DeviceInfo di = device_info();
+    int64_t want = (n + 255) / 256;
+    int grid = (int)(want < (int64_t)di.sms * 8 ? want : (int64_t)di.sms * 8);
+    if (grid < 1) grid = 1;
+    pixel_keys<<<grid, 256, 0, s>>>(rgb, n, keys, weights, n_out);
+    return cudaGetLastError() == cudaSuccess ? KQ_OK : KQ_ECUDA;
+}
+
+int launch_histogram_strided(const uint8_t *rgb, int32_t h, int32_t w, int64_t pitch, int32_t stride, uint32_t *keys,
+                             uint32_t *weights, int32_t cap, int32_t *n_unique, void *ws, const Layout &L,
+                             cudaStream_t s)
+{
+    uint32_t *cnt = at<uint32_t>(ws, L.hist_cnt);
+    uint32_t *bits = at<uint32_t>(ws, L.hist_bits);
+    uint32_t *chunk_tot = at<uint32_t>(ws, L.hist_chunk);
+    Ctl *ctl = at<Ctl>(ws, L.ctl);
+    const DeviceInfo di = device_info();
+    const int64_t total = (int64_t)((h + stride - 1) / stride) * ((w + stride - 1) / stride);
+    int64_t want = (total + kCountBlock - 1) / kCountBlock;
+    int grid = (int)(want < (int64_t)di.sms * 8 ? want : (int64_t)di.sms * 8);
+    if (grid < 1) grid = 1;
+    if (total > 0) hist_count_strided<<<grid, kCountBlock, 0, s>>>(rgb, h, w, pitch, stride, cnt, bits);
+    uint32_t *chunk_base = chunk_tot + kHistChunks;
+    hist_chunks<<<kHistChunks, kEmitBlock, 0, s>>>(bits, chunk_tot);
+    hist_bases<<<1, kBaseBlock, 0, s>>>(chunk_tot, chunk_base, cap, n_unique, ctl);
+    hist_emit<<<kHistChunks, kEmitBlock, 0, s>>>(bits, cnt, chunk_base, keys, weights, cap);
+    return cudaGetLastError() == cudaSuccess ? KQ_OK : KQ_ECUDA;
+}
 
 int launch_histogram(const uint8_t *rgb, int64_t n, uint32_t *keys, uint32_t *weights, int32_t cap, int32_t *n_unique,
                      void *ws, const Layout &L, cudaStream_t s)

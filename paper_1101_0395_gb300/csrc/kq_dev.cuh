@@ -343,6 +343,11 @@ int launch_lloyd(const uint32_t *keys, const uint32_t *w, const int32_t *n_uniqu
                  double *sse_hist, void *ws, const Layout &L, cudaStream_t s, int skip_if_n_le);
 int launch_seed(const uint32_t *keys, const uint32_t *w, const int32_t *n_unique, int K, int scheme, uint64_t seed,
                 const kq_seed_params &p, double *centers, void *ws, const Layout &L, cudaStream_t s);
+int launch_histogram_strided(const uint8_t *rgb, int32_t h, int32_t w, int64_t pitch, int32_t stride, uint32_t *keys,
+                             uint32_t *weights, int32_t cap, int32_t *n_unique, void *ws, const Layout &L,
+                             cudaStream_t s);
+int launch_pixel_keys(const uint8_t *rgb, int64_t n, uint32_t *keys, uint32_t *weights, int32_t *n_out,
+                      cudaStream_t s);
 int launch_map(const uint8_t *rgb, int64_t n, const uint32_t *keys, const uint32_t *w, const int32_t *n_unique,
                const uint8_t *palette, int K, uint8_t *idx, int64_t *sse_num, void *ws, const Layout &L,
                cudaStream_t s);

@@ -48,7 +48,7 @@ struct LloydShared {
     double c64[kMaxK * 3];
     unsigned long long sum[kMaxK * 4];
     uint32_t sum32[kMaxK * 4];  // used instead of sum when the block's sums fit 32 bits
-    uint32_t row[2][kMaxK];
+    uint32_t row[2][kMaxK];     // rows being ranked (build_rows_rank)
     float red_f[kLloydBlock / 32];
     unsigned long long red_u[kLloydBlock / 32];
     double sse_i;
@@ -56,10 +56,78 @@ struct LloydShared {
     int narrow;
 };
 
+// Ascending bitonic sort of the 32 * EPL values a warp holds, element e = lane * EPL
+// + j in v[j] of that lane: pairs more than EPL apart are exchanged by shuffles,
+// the others inside the lane.
+template <int EPL>
+__device__ __forceinline__ void warp_bitonic_sort(uint32_t (&v)[EPL], int lane)
+{
+    constexpr int P = 32 * EPL;
+#pragma unroll
+    for (int size = 2; size <= P; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            if (stride >= EPL) {
+#pragma unroll
+                for (int j = 0; j < EPL; ++j) {
+                    const uint32_t o = __shfl_xor_sync(0xffffffffu, v[j], stride / EPL);
+                    const int e = lane * EPL + j;
+                    const bool up = (e & size) == 0, low = (e & stride) == 0;
+                    v[j] = (low == up) ? min(v[j], o) : max(v[j], o);
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < EPL; ++j) {
+                    if ((j & stride) == 0) {
+                        const int e = lane * EPL + j;
+                        const bool up = (e & size) == 0;
+                        const uint32_t x = v[j], y = v[j + stride];
+                        const bool sw = (x > y) == up;
+                        v[j] = sw ? y : x;
+                        v[j + stride] = sw ? x : y;
+                    }
+                }
+            }
+        }
+    }
+}
+
+// Rows p = b + G m (m = 0, 1, ...) of the sorted centre-distance table, one row per
+// warp at a time: entry (distance bits with the low 8 cleared) | index, sorted
+// ascending by a warp-wide bitonic network (every entry is distinct).
+template <int EPL>
+__device__ __forceinline__ void build_rows_t(const LloydShared &sh, int K, int b, int G, uint32_t *rows)
+{
+    constexpr int kWarpsB = kLloydBlock / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int Kp = (K + 3) & ~3;
+    for (int m = warp; b + G * m < K; m += kWarpsB) {
+        const int p = b + G * m;
+        const float4 cp = sh.c[p];
+        uint32_t v[EPL];
+#pragma unroll
+        for (int j = 0; j < EPL; ++j) {
+            const int t = lane * EPL + j;
+            v[j] = 0xFFFFFFFFu;
+            if (t < K) {
+                const float4 ct = sh.c[t];
+                const float d = dist3(cp.x, cp.y, cp.z, ct.x, ct.y, ct.z);
+                v[j] = (__float_as_uint(d) & 0xFFFFFF00u) | (uint32_t)t;
+            }
+        }
+        warp_bitonic_sort<EPL>(v, lane);
+#pragma unroll
+        for (int j = 0; j < EPL; ++j) {
+            const int e = lane * EPL + j;
+            if (e < Kp) rows[(size_t)p * Kp + e] = e < K ? v[j] : kPadEntry;
+        }
+    }
+}
+
 // Rows p = b, b + G, b + 2G, ... of the sorted centre-distance table; the two
 // halves of the block build two rows at once.  Entry rank = number of smaller
 // packed entries (the index in the low byte makes every entry distinct).
-__device__ __forceinline__ void build_rows(LloydShared &sh, int K, int b, int G, uint32_t *rows)
+__device__ __forceinline__ void build_rows_rank(LloydShared &sh, int K, int b, int G, uint32_t *rows)
 {
     constexpr int kHalf = kLloydBlock / 2;  // >= kMaxK
     const int Kp = (K + 3) & ~3;
@@ -94,6 +162,18 @@ __device__ __forceinline__ void build_rows(LloydShared &sh, int K, int b, int G,
         }
         __syncthreads();
     }
+}
+
+// Few rows per block (K <= 2G, the whole-grid launch): the rank count above, two rows
+// at once over all threads, has the shortest latency.  Many rows per block (block
+// groups of a batch): one row per warp, sorted by the bitonic network.
+__device__ __forceinline__ void build_rows(LloydShared &sh, int K, int b, int G, uint32_t *rows)
+{
+    if (K <= 2 * G) build_rows_rank(sh, K, b, G, rows);
+    else if (K <= 32) build_rows_t<1>(sh, K, b, G, rows);
+    else if (K <= 64) build_rows_t<2>(sh, K, b, G, rows);
+    else if (K <= 128) build_rows_t<4>(sh, K, b, G, rows);
+    else build_rows_t<8>(sh, K, b, G, rows);
 }
 
 __device__ __forceinline__ void set_centre(LloydShared &sh, int k, float4 c)
@@ -136,6 +216,73 @@ __device__ __forceinline__ void dense_argmin(const LloydShared &sh, int K, float
         if (d < best) {
             best = d;
             arg = k;
+        }
+    }
+}
+
+// dense_argmin for two points at once: each group of eight centres is loaded from
+// shared memory once (16-byte loads of the per-channel arrays) and used for both
+// points, which also gives the scheduler two independent chains.  Per point the
+// distances, the order of the comparisons and so the results are those of
+// dense_argmin.
+__device__ __forceinline__ void dense_argmin2(const LloydShared &sh, int K, float x0, float y0, float z0, float x1,
+                                              float y1, float z1, float &best0, int &arg0, float &best1, int &arg1)
+{
+    best0 = best1 = __int_as_float(0x7f800000);
+    int bg0 = -1, bg1 = -1;
+    int k0 = 0;
+    for (; k0 + 8 <= K; k0 += 8) {
+        const float4 xa = *reinterpret_cast<const float4 *>(&sh.cx[k0]);
+        const float4 xb = *reinterpret_cast<const float4 *>(&sh.cx[k0 + 4]);
+        const float4 ya = *reinterpret_cast<const float4 *>(&sh.cy[k0]);
+        const float4 yb = *reinterpret_cast<const float4 *>(&sh.cy[k0 + 4]);
+        const float4 za = *reinterpret_cast<const float4 *>(&sh.cz[k0]);
+        const float4 zb = *reinterpret_cast<const float4 *>(&sh.cz[k0 + 4]);
+        const float cx[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
+        const float cy[8] = {ya.x, ya.y, ya.z, ya.w, yb.x, yb.y, yb.z, yb.w};
+        const float cz[8] = {za.x, za.y, za.z, za.w, zb.x, zb.y, zb.z, zb.w};
+        float d0[8], d1[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            d0[j] = dist3(x0, y0, z0, cx[j], cy[j], cz[j]);
+            d1[j] = dist3(x1, y1, z1, cx[j], cy[j], cz[j]);
+        }
+        const float m0 =
+            fminf(fminf(fminf(d0[0], d0[1]), fminf(d0[2], d0[3])), fminf(fminf(d0[4], d0[5]), fminf(d0[6], d0[7])));
+        const float m1 =
+            fminf(fminf(fminf(d1[0], d1[1]), fminf(d1[2], d1[3])), fminf(fminf(d1[4], d1[5]), fminf(d1[6], d1[7])));
+        if (m0 < best0) {
+            best0 = m0;
+            bg0 = k0;
+        }
+        if (m1 < best1) {
+            best1 = m1;
+            bg1 = k0;
+        }
+    }
+    arg0 = 0;
+    arg1 = 0;
+    if (bg0 >= 0) {
+#pragma unroll
+        for (int j = 7; j >= 0; --j)
+            if (dist3(x0, y0, z0, sh.cx[bg0 + j], sh.cy[bg0 + j], sh.cz[bg0 + j]) == best0) arg0 = bg0 + j;
+    }
+    if (bg1 >= 0) {
+#pragma unroll
+        for (int j = 7; j >= 0; --j)
+            if (dist3(x1, y1, z1, sh.cx[bg1 + j], sh.cy[bg1 + j], sh.cz[bg1 + j]) == best1) arg1 = bg1 + j;
+    }
+    for (int k = k0; k < K; ++k) {
+        const float cxk = sh.cx[k], cyk = sh.cy[k], czk = sh.cz[k];
+        const float e0 = dist3(x0, y0, z0, cxk, cyk, czk);
+        const float e1 = dist3(x1, y1, z1, cxk, cyk, czk);
+        if (e0 < best0) {
+            best0 = e0;
+            arg0 = k;
+        }
+        if (e1 < best1) {
+            best1 = e1;
+            arg1 = k;
         }
     }
 }
@@ -264,7 +411,42 @@ __device__ __forceinline__ void lloyd_body(const LloydArgs &a, LloydShared &sh, 
         __syncthreads();
         float sse32 = 0.f;
         unsigned long long ndc = 0ull;
-        for (int64_t c = b + (int64_t)G * warp; c < nch; c += (int64_t)G * kWarps) {
+        // Full search (first pass, or no pruning): chunks c and c + S in one step, two
+        // points per lane.  The SSE is still added in chunk order, as in the pruned loop.
+        const int64_t S = (int64_t)G * kWarps;
+        for (int64_t c = b + (int64_t)G * warp; !use_prev && c < nch; c += 2 * S) {
+            const int64_t c1 = c + S;
+            const int64_t i0 = c * 32 + lane, i1 = c1 * 32 + lane;
+            const bool act0 = i0 < n, act1 = c1 < nch && i1 < n;
+            uint32_t k0 = 0u, w0 = 0u, k1 = 0u, w1 = 0u;
+            if (act0) {
+                k0 = a.keys[i0];
+                w0 = a.w[i0];
+            }
+            if (act1) {
+                k1 = a.keys[i1];
+                w1 = a.w[i1];
+            }
+            float b0, b1;
+            int g0, g1;
+            dense_argmin2(sh, K, (float)key_r(k0), (float)key_g(k0), (float)key_b(k0), (float)key_r(k1),
+                          (float)key_g(k1), (float)key_b(k1), b0, g0, b1, g1);
+            if (act0) {
+                a.labels[i0] = (uint8_t)g0;
+                sse32 = __fadd_rn(sse32, __fmul_rn((float)w0, b0));
+                ndc += (unsigned long long)K;
+            }
+            warp_accumulate(sh, narrow, act0, g0, w0, k0);
+            if (c1 < nch) {
+                if (act1) {
+                    a.labels[i1] = (uint8_t)g1;
+                    sse32 = __fadd_rn(sse32, __fmul_rn((float)w1, b1));
+                    ndc += (unsigned long long)K;
+                }
+                warp_accumulate(sh, narrow, act1, g1, w1, k1);
+            }
+        }
+        for (int64_t c = b + (int64_t)G * warp; use_prev && c < nch; c += (int64_t)G * kWarps) {
             const int64_t i = c * 32 + lane;
             const bool active = i < n;
             uint32_t key = 0u, w = 0u;

@@ -2,10 +2,13 @@
 // the squared-error sum behind the MSE of Section 3.1 (Eq. 2).
 //
 // Each unique colour is matched to the palette once (map_lut), writing its index
-// into a 2^24-entry byte table at its key and adding w * d to the error sum; the
-// pixel stream (map_pixels) then reads 48 bytes per 16 pixels, looks each key up
-// in the table (16 MiB, resident in L2) and writes 16 indices with one 16-byte
-// store.  Distances between 8-bit colours are exact integers below 2^18.
+// into a 2^24-entry byte table and adding w * d to the error sum; the pixel stream
+// (map_pixels) then reads 48 bytes per 16 pixels, looks each colour up in the
+// table (16 MiB, resident in L2) and writes 16 indices with one 16-byte store.
+// The table is laid out in 4 x 4 x 4 colour blocks (lut_slot), so that one 32-byte
+// L2 sector holds a 2 x 4 x 4 neighbourhood of colours instead of 32 values of B:
+// neighbouring pixels of an image touch far fewer sectors.  Distances between
+// 8-bit colours are exact integers below 2^18.
 #include "kq_dev.cuh"
 
 namespace kq {
@@ -13,6 +16,15 @@ namespace {
 
 constexpr int kLutBlock = 256;
 constexpr int kPixBlock = 256;
+
+// Table slot of colour (R << 16) | (G << 8) | B: the 4 x 4 x 4 block
+// (R >> 2, G >> 2, B >> 2) times 64, plus (R & 3) * 16 + (G & 3) * 4 + (B & 3).
+// A permutation of 0 .. 2^24 - 1.
+__device__ __forceinline__ uint32_t lut_slot(uint32_t key)
+{
+    return (key & 0xFC0000u) | ((key & 0xFC00u) << 2) | ((key & 0xFCu) << 4) | ((key >> 12) & 0x30u) |
+           ((key >> 6) & 0xCu) | (key & 3u);
+}
 
 // Nearest palette entry of each unique colour.  With colours as byte vectors,
 // |x - p|^2 = |x|^2 + |p|^2 - 2 x.p is an exact integer below 2^18, the dot product
@@ -45,10 +57,10 @@ __global__ void __launch_bounds__(kLutBlock) map_lut(const uint32_t *__restrict_
             ma = min(ma, ba + pk.y - (__dp4a(ka, pk.x, 0u) << 9));
             mb = min(mb, bbv + pk.y - (__dp4a(kb, pk.x, 0u) << 9));
         }
-        lut[ka] = (uint8_t)(ma & 0xFFu);
+        lut[lut_slot(ka)] = (uint8_t)(ma & 0xFFu);
         acc += (unsigned long long)w[i0] * (ma >> 8);
         if (two) {
-            lut[kb] = (uint8_t)(mb & 0xFFu);
+            lut[lut_slot(kb)] = (uint8_t)(mb & 0xFFu);
             acc += (unsigned long long)w[i0 + 1] * (mb >> 8);
         }
     }
@@ -76,8 +88,8 @@ __device__ __forceinline__ uint32_t group_key(const uint32_t (&w)[12])
 template <int I>
 __device__ __forceinline__ uint32_t lut4(const uint8_t *lut, const uint32_t (&w)[12])
 {
-    return (uint32_t)lut[group_key<I>(w)] | ((uint32_t)lut[group_key<I + 1>(w)] << 8) |
-           ((uint32_t)lut[group_key<I + 2>(w)] << 16) | ((uint32_t)lut[group_key<I + 3>(w)] << 24);
+    return (uint32_t)lut[lut_slot(group_key<I>(w))] | ((uint32_t)lut[lut_slot(group_key<I + 1>(w))] << 8) |
+           ((uint32_t)lut[lut_slot(group_key<I + 2>(w))] << 16) | ((uint32_t)lut[lut_slot(group_key<I + 3>(w))] << 24);
 }
 
 template <bool kVecOut>
@@ -88,8 +100,8 @@ __global__ void __launch_bounds__(kPixBlock) map_pixels(const uint8_t *__restric
     const int64_t nth = (int64_t)gridDim.x * kPixBlock;
     const int64_t ngroups = (n - head) / 16;
     const int64_t tail0 = head + ngroups * 16;
-    for (int64_t p = tid; p < head; p += nth) idx[p] = lut[pixel_key(rgb, p)];
-    for (int64_t p = tail0 + tid; p < n; p += nth) idx[p] = lut[pixel_key(rgb, p)];
+    for (int64_t p = tid; p < head; p += nth) idx[p] = lut[lut_slot(pixel_key(rgb, p))];
+    for (int64_t p = tail0 + tid; p < n; p += nth) idx[p] = lut[lut_slot(pixel_key(rgb, p))];
     const uint4 *g = reinterpret_cast<const uint4 *>(rgb + 3 * head);
     for (int64_t gi = tid; gi < ngroups; gi += nth) {
         const uint4 a = __ldcs(g + 3 * gi), b = __ldcs(g + 3 * gi + 1), c = __ldcs(g + 3 * gi + 2);

@@ -285,6 +285,7 @@ struct ClusterArgs {
     int ctas;       // cluster size
     uint64_t seed;
     double *centers;
+    Ctl *ctl;
 };
 
 struct ClusterShared {
@@ -723,6 +724,7 @@ int launch_seed(const uint32_t *keys, const uint32_t *w, const int32_t *n_unique
             ca.ctas = ctas;
             ca.seed = seed;
             ca.centers = centers;
+            ca.ctl = ctl;
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(ctas);
             cfg.blockDim = dim3(kClBlock);

@@ -67,6 +67,9 @@ _SIGS = {
     "kq_map": (C.c_int, [_vp, C.c_int64, _vp, _vp, _vp, _vp, C.c_int32, _vp, _vp, _vp, C.c_size_t, _vp]),
     "kq_lloyd_noalloc": (C.c_int, [_vp, _vp, _vp, C.c_int32, _vp, C.c_double, C.c_int32, C.c_uint32, _vp, _vp,
                                    _vp, _vp, _vp]),
+    "kq_pixel_keys": (C.c_int, [_vp, C.c_int64, _vp, _vp, _vp, _vp]),
+    "kq_histogram_strided": (C.c_int, [_vp, C.c_int32, C.c_int32, C.c_int64, C.c_int32, _vp, _vp, C.c_int32, _vp,
+                                       _vp, C.c_size_t, _vp]),
     "kq_status_read": (C.c_int, [_vp, C.POINTER(C.c_int32), _vp]),
     "kq_status_clear": (C.c_int, [_vp, _vp]),
     "kq_strerror": (C.c_char_p, [C.c_int]),
@@ -273,6 +276,24 @@ class Quantizer:
                           + launches("kq_map", n))
         return Result(idx=idx, palette=pal.view(K, 3), centers=c.view(K, 3), n_unique=self.n_unique,
                       sse_num=self.sse_num, stats=self.stats)
+
+
+def kq_histogram_strided(rgb: torch.Tensor, height: int, width: int, stride: int, keys: torch.Tensor,
+                         weights: torch.Tensor, n_unique: torch.Tensor, ws: torch.Tensor, pitch: Optional[int] = None,
+                         stream=None) -> None:
+    """Histogram of the pixels (x, y) with x, y multiples of `stride` (Section 2.2)."""
+    pitch = 3 * width if pitch is None else pitch
+    _check("kq_histogram_strided", lib().kq_histogram_strided(
+        _ptr(rgb) if height * width else None, height, width, pitch, stride, _ptr(keys), _ptr(weights),
+        keys.numel(), _ptr(n_unique), _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)))
+
+
+def kq_pixel_keys(rgb: torch.Tensor, keys: torch.Tensor, weights: Optional[torch.Tensor] = None,
+                  n_out: Optional[torch.Tensor] = None, stream=None) -> None:
+    """Every pixel as its own point (the k-means baseline of Table 1)."""
+    n = rgb.numel() // 3
+    _check("kq_pixel_keys", lib().kq_pixel_keys(_ptr(rgb) if n else None, n, _ptr(keys), _ptr(weights), _ptr(n_out),
+                                                _stream(stream)))
 
 
 def kq_batch_scratch_bytes(capacity: int) -> int:

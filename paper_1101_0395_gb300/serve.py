@@ -184,7 +184,7 @@ class Server:
             if not batch:
                 break
             slot = self.free_slots.popleft()
-            handle = self.backend.launch(slot, batch)
+            handle = self.backend.launch(slot, batch, alone=not self.running)
             self.running.append(Wave(slot, batch, handle))
             self.waves += 1
             self.max_running = max(self.max_running, len(self.running))
@@ -244,7 +244,10 @@ class CudaBackend:
 
     OUT = ("idx", "palette", "centers", "result")
 
-    def __init__(self, cluster: int = 1, split_pixels: int = 1 << 62, device=None):
+    def __init__(self, cluster: int = 1, split_pixels: int = 1 << 62, device=None, solo_max_pixels: int = 0):
+        """solo_max_pixels > 0: a wave of one request that finds the device idle runs
+        on the whole GPU through the four single-image calls (lowest latency under
+        light load) instead of one block group of kq_batch_run."""
         import torch
 
         from . import kq
@@ -252,6 +255,8 @@ class CudaBackend:
         self.torch, self.kq = torch, kq
         self.device = torch.device("cuda") if device is None else torch.device(device)
         self.cfg = kq.BatchConfig(int(cluster), 0, int(split_pixels))
+        self.solo_max_pixels = int(solo_max_pixels)
+        self.solo_waves = 0
 
     def scratch_bytes(self, cap: int) -> int:
         return self.kq.kq_batch_scratch_bytes(cap)
@@ -271,6 +276,13 @@ class CudaBackend:
         self.events = [torch.cuda.Event() for _ in range(streams)]
         self.h2d_bytes = 0
         self.d2h_bytes = 0
+        self.solo = None
+        if self.solo_max_pixels > 0:
+            self.solo = PlainBackend(self.solo_max_pixels, device=self.device)
+            self.solo.setup(0, 1, 1)
+        # the workspaces were zero-filled on the current stream; the waves run on
+        # their own streams
+        torch.cuda.current_stream(self.device).synchronize()
 
     def _pinned(self, r: "Request"):
         t = r.rgb
@@ -278,8 +290,13 @@ class CudaBackend:
             t = self.torch.from_numpy(np.ascontiguousarray(t).reshape(-1))
         return t.reshape(-1)
 
-    def launch(self, slot: int, batch: List[Request]):
+    def launch(self, slot: int, batch: List[Request], alone: bool = False):
         torch, kq = self.torch, self.kq
+        if self.solo is not None and alone and len(batch) == 1 and batch[0].n_pixels <= self.solo_max_pixels:
+            self.solo_waves += 1
+            self.h2d_bytes += 3 * batch[0].n_pixels
+            self.d2h_bytes += batch[0].n_pixels + 3 * batch[0].K
+            return ("solo", self.solo.launch(0, batch))
         s = self.streams[slot]
         base = self.pool.data_ptr()
         items = np.zeros(len(batch), dtype=kq.BATCH_ITEM_DTYPE)
@@ -327,10 +344,15 @@ class CudaBackend:
         return (slot, ev, outs)
 
     def done(self, handle) -> bool:
+        if handle[0] == "solo":
+            return self.solo.done(handle[1])
         return handle[1].query()
 
     def collect(self, handle, batch: List[Request]) -> None:
         kq = self.kq
+        if handle[0] == "solo":
+            self.solo.collect(handle[1], batch)
+            return
         stage = self.h_out[handle[0]].numpy()
         for r, o in zip(batch, handle[2]):
             def get(name):
@@ -367,8 +389,10 @@ class PlainBackend:
         self.events = [torch.cuda.Event() for _ in range(streams)]
         self.h_idx = [torch.empty(self.max_pixels, dtype=torch.uint8).pin_memory() for _ in range(streams)]
         self.h_small = [torch.empty(8192, dtype=torch.uint8).pin_memory() for _ in range(streams)]
+        # the Quantizers' workspaces were zero-filled on the current stream
+        torch.cuda.current_stream(self.device).synchronize()
 
-    def launch(self, slot: int, batch: List[Request]):
+    def launch(self, slot: int, batch: List[Request], alone: bool = False):
         torch = self.torch
         s = self.streams[slot]
         q = self.q[slot]

@@ -16,7 +16,8 @@ def test_exports_every_declared_symbol():
     assert set(names) == {"kq_workspace_size", "kq_workspace_init", "kq_histogram", "kq_seed", "kq_lloyd", "kq_map",
                           "kq_lloyd_noalloc", "kq_status_read", "kq_status_clear", "kq_strerror",
                           "kq_batch_scratch_bytes", "kq_batch_workspace_size", "kq_batch_max_cluster",
-                          "kq_batch_plan", "kq_batch_run", "kq_batch_tune"}
+                          "kq_batch_plan", "kq_batch_run", "kq_batch_tune", "kq_pixel_keys",
+                          "kq_histogram_strided"}
     L = kq.lib()
     for n in names:
         assert getattr(L, n) is not None
@@ -116,3 +117,10 @@ def test_batch_run_rejects_bad_arguments_on_the_host():
     bad = kq.BatchConfig(6, 0, 0)
     assert L.kq_batch_run(p, 4, p, 0, C.byref(bad), WS, size, None) == kq.KQ_EINVAL
     assert L.kq_batch_tune(None, p, 4, p, None, None, None, WS, size, None) == kq.KQ_EINVAL
+    size2 = kq.kq_workspace_size(1000, 256)
+    assert L.kq_histogram_strided(p, 10, 10, 29, 2, p, p, 10, p, WS, size2, None) == kq.KQ_EINVAL  # pitch < 3 w
+    assert L.kq_histogram_strided(p, 10, 10, 30, 0, p, p, 10, p, WS, size2, None) == kq.KQ_EINVAL  # stride 0
+    assert L.kq_histogram_strided(None, 10, 10, 30, 2, p, p, 10, p, WS, size2, None) == kq.KQ_EINVAL
+    assert L.kq_pixel_keys(None, 10, p, None, None, None) == kq.KQ_EINVAL
+    assert L.kq_pixel_keys(p, -1, p, None, None, None) == kq.KQ_EINVAL
+    assert L.kq_pixel_keys(p, 1 << 31, p, None, None, None) == kq.KQ_EINVAL

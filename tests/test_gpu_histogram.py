@@ -109,3 +109,28 @@ def test_histogram_invalid_arguments():
     with pytest.raises(kq.KqError) as e:
         kq.kq_histogram(torch.zeros(48, dtype=torch.uint8, device="cuda"), t, t, t[:1], ws[:1024])
     assert e.value.status == kq.KQ_EINVAL
+
+
+@pytest.mark.parametrize("h,w,stride,pad", [(101, 77, 2, 0), (64, 64, 2, 5), (37, 90, 3, 2), (50, 51, 1, 0),
+                                            (1, 1, 2, 0), (0, 10, 2, 0)])
+def test_strided_histogram_matches_oracle_on_the_subsample(h, w, stride, pad):
+    """Section 2.2's 2:1 subsampling: the histogram of the pixels (x, y) with x, y
+    multiples of the stride, here with rows `pad` pixels longer than the image."""
+    require_cuda()
+    img = synth.image(max(h, 1), w + pad, 6, 12.0, 5.0, 77 + h)[:h] if h else np.zeros((0, w + pad, 3), np.uint8)
+    pitch = 3 * (w + pad)
+    sub = img[::stride, :w:stride]
+    keys_o, w_o = oracle.histogram(sub.reshape(-1, 3)) if sub.size else (np.zeros(0, np.uint32),) * 2
+    cap = max(1, h * w)
+    keys = torch.zeros(cap, dtype=torch.int32, device="cuda")
+    wts = torch.zeros(cap, dtype=torch.int32, device="cuda")
+    nu = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ws = torch.zeros(kq.kq_workspace_size(cap, 256), dtype=torch.uint8, device="cuda")
+    rgb = to_dev(np.ascontiguousarray(img).reshape(-1)) if img.size else torch.zeros(1, dtype=torch.uint8,
+                                                                                      device="cuda")
+    kq.kq_histogram_strided(rgb, h, w, stride, keys, wts, nu, ws, pitch=pitch)
+    torch.cuda.synchronize()
+    n = int(nu.item())
+    assert n == keys_o.size
+    assert np.array_equal(u32(keys[:n]), keys_o) and np.array_equal(u32(wts[:n]), w_o)
+    assert int(u32(wts[:n]).sum()) == ((h + stride - 1) // stride) * ((w + stride - 1) // stride)

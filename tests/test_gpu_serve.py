@@ -54,3 +54,35 @@ def test_same_result_alone_and_in_the_mix():
         assert r.result["n_unique"] == keys.size
         oidx, osse = oracle.map_pixels(img, r.palette)
         assert np.array_equal(r.idx, oidx) and r.result["sse_num"] == osse
+
+
+def test_lone_requests_take_the_whole_gpu_and_agree_within_tolerance():
+    """With solo mode a request that finds the device idle runs through the four
+    single-image calls on the whole GPU; in a busy mix it runs in a batch wave.
+    Both are the same method: the final MSE agrees within 1e-5 relative, and when
+    the stop test fires at the same pass the palettes are equal and the centres
+    agree within 1e-3."""
+    require_cuda()
+    C = kq.kq_batch_max_cluster()
+    max_px = max(h * w for h, w, _, _ in SIZES)
+    one = max(serve.request_layout(h * w, K, kq.kq_batch_scratch_bytes)[1] for h, w, K, _ in SIZES)
+    srv = serve.Server(serve.CudaBackend(min(C, 4), 30000, solo_max_pixels=max_px), 4 * one, streams=2,
+                       max_wave=4)
+    mix = _requests()
+    for r in mix:
+        r.arrival = 0.0
+    serve.run_trace(srv, mix)
+    alone_be = serve.CudaBackend(min(C, 4), 30000, solo_max_pixels=max_px)
+    alone_srv = serve.Server(alone_be, one, streams=1, max_wave=1)
+    for r in mix:
+        a = serve.Request(rid=r.rid, rgb=r.rgb, K=r.K, scheme=r.scheme, seed=r.seed)
+        alone_srv.submit(a)
+        alone_srv.drain()
+        assert a.result["status"] == kq.KQ_OK and r.result["status"] == kq.KQ_OK
+        assert a.result["n_unique"] == r.result["n_unique"]
+        sa, sm = int(a.result["sse_num"]), int(r.result["sse_num"])
+        assert abs(sa - sm) <= 1e-5 * max(sa, 1)
+        if a.result["lloyd"]["iters"] == r.result["lloyd"]["iters"]:
+            assert np.array_equal(a.palette, r.palette)
+            assert np.max(np.abs(a.centers - r.centers)) <= 1e-3
+    assert alone_be.solo_waves == len(mix)

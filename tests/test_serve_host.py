@@ -20,7 +20,7 @@ class FakeBackend:
     def setup(self, pool_bytes, streams, max_wave):
         self.pool_bytes, self.n_streams, self.max_wave = pool_bytes, streams, max_wave
 
-    def launch(self, slot, batch):
+    def launch(self, slot, batch, alone=False):
         self.launched.append((slot, [r.rid for r in batch], self.server.arena.in_use))
         return {"polls": 0, "slot": slot}
 
