@@ -757,12 +757,23 @@ def run_gpu(args, rank, world, local) -> None:
                                % (props.multi_processor_count, sm_max),
                 "algorithmic": "%d FLOP per distance x NDC %d" % (FLOP_PER_DIST, st["ndc"])}
     elif dom == 1:
-        # seeding: each of K rounds reads key, weight and D^2 and writes D^2 per unique colour
-        byts = 16.0 * n_unique * K
-        achieved = byts / (stage_mean[1] * 1e-3) / 1e9
-        roof = {"kernel": "seed_far (kq_seed, k-means++)", "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
-                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None, "peak_source": "MEASURED_PEAKS hbm_gbs",
-                "algorithmic": "16 B per unique colour per round x %d rounds" % K}
+        # k-means++ in one thread-block cluster: K sequential rounds, each refreshing the
+        # exact integer D^2 of every unique colour (one dp4a distance plus ~7 integer
+        # operations: 8 ALU operations per colour and round) between two cluster barriers.
+        # The slice lives in shared memory, so DRAM is idle; the barrier per round, not a
+        # unit's throughput, sets the time.  Reported against the 32-bit ALU peak.
+        ops = 8.0 * n_unique * K
+        achieved = ops / (stage_mean[1] * 1e-3) / 1e12
+        alu_peak = fp32_peak / 2.0  # one integer operation per lane per clock
+        roof = {"kernel": "seed_far_cluster (kq_seed, k-means++: 16-CTA cluster, one barrier per round)",
+                "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
+                "frac": achieved / alu_peak, "traffic": 818432,
+                "peak_source": "derived: %d SMs x 128 lanes x 1 op x %.0f MHz (max SM clock, measured)"
+                               % (props.multi_processor_count, sm_max),
+                "algorithmic": "8 integer ops per unique colour per round x %d rounds (latency-bound: "
+                               "cluster barrier per round)" % K,
+                "traffic_source": "profiles/seed_far_cluster_lloyd_kernel_paper512_k256.txt (dram read+write "
+                                  "per launch)"}
     else:
         byts = (3.0 * n + 8.0 * n_unique) if dom == 0 else (4.0 * n + 8.0 * n_unique)
         achieved = byts / (stage_mean[dom] * 1e-3) / 1e9

@@ -69,7 +69,10 @@ typedef enum {
     KQ_INIT_VAR = 4, /* maximum variance: medians of K groups on the widest channel */
     KQ_INIT_SFF = 5, /* subset farthest first on ceil(2 K ln K) random colours */
     KQ_INIT_KPP = 6, /* k-means++ (D^2 sampling, pixel-weighted) */
-    KQ_INIT_USER = 7
+    KQ_INIT_USER = 7,
+    KQ_INIT_WU = 8   /* Wu's greedy orthogonal bipartitioning (Section 3.3; the WSM-WU initializer):
+                        32^3 cells, the box of largest weighted variance split by the cut minimizing
+                        the sum of the halves' variances, centres = box means */
 } kq_init;
 
 /* Parameters the paper leaves open; pass NULL for the defaults in brackets. */

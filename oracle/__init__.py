@@ -15,7 +15,8 @@ Functions and the passage each follows:
   palette     -- rounding of the final centres to 8-bit colours
   map_pixels  -- Section 1 / 2.1 pixel mapping by full palette search
   mse, psnr   -- Section 3.1, Eqs. 2 and 3
-  seed        -- Section 2.3 generic initialization schemes
+  seed        -- Section 2.3 generic initialization schemes, and WU (Section 3.3)
+  wu          -- Wu's greedy orthogonal bipartitioning (Section 3.3, WSM-WU)
 
 Parity status: every function above is pinned by ``tests/test_oracle_pins.py``
 (closed forms, brute force on tiny inputs, invariants, library routines).
@@ -32,7 +33,7 @@ import numpy as np
 
 from . import build as _build
 
-SCHEMES = {"FGY": 0, "LBG": 1, "MMX": 2, "DEN": 3, "VAR": 4, "SFF": 5, "KPP": 6}
+SCHEMES = {"FGY": 0, "LBG": 1, "MMX": 2, "DEN": 3, "VAR": 4, "SFF": 5, "KPP": 6, "WU": 8}
 
 _libs: Dict[str, C.CDLL] = {}
 _variant = "serial"
@@ -100,6 +101,8 @@ def lib() -> C.CDLL:
         L.or_sff_size.argtypes = [C.c_int64, C.c_int]
         L.or_var_channel.restype = C.c_int
         L.or_var_channel.argtypes = [_u32p, _u32p, C.c_int64]
+        L.or_wu.restype = C.c_int
+        L.or_wu.argtypes = [_u32p, _u32p, C.c_int64, C.c_int, _f64p]
         L.or_den_quota.restype = None
         L.or_den_quota.argtypes = [_i64p, _i64p, C.c_int, _i64p]
         _libs[_variant] = L
@@ -228,6 +231,16 @@ def sff_size(n: int, K: int) -> int:
 def var_channel(keys: np.ndarray, w: np.ndarray) -> int:
     keys = np.ascontiguousarray(keys, dtype=np.uint32)
     return int(lib().or_var_channel(keys, np.ascontiguousarray(w, dtype=np.uint32), keys.size))
+
+
+def wu(keys: np.ndarray, w: np.ndarray, K: int) -> Tuple[np.ndarray, int]:
+    """Wu's greedy orthogonal bipartitioning: (K x 3 box means, boxes made)."""
+    keys = np.ascontiguousarray(keys, dtype=np.uint32)
+    c = np.zeros(K * 3, dtype=np.float64)
+    nb = lib().or_wu(keys, np.ascontiguousarray(w, dtype=np.uint32), keys.size, int(K), c)
+    if nb < 0:
+        raise ValueError("oracle wu failed")
+    return c.reshape(K, 3), int(nb)
 
 
 def den_quota(cellw: np.ndarray, celln: np.ndarray, K: int) -> np.ndarray:

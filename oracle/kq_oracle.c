@@ -36,7 +36,7 @@
 
 #define OR_API __attribute__((visibility("default")))
 
-enum { OR_FGY = 0, OR_LBG = 1, OR_MMX = 2, OR_DEN = 3, OR_VAR = 4, OR_SFF = 5, OR_KPP = 6 };
+enum { OR_FGY = 0, OR_LBG = 1, OR_MMX = 2, OR_DEN = 3, OR_VAR = 4, OR_SFF = 5, OR_KPP = 6, OR_WU = 8 };
 
 /* ------------------------------------------------------------------------- */
 /* Random numbers: SplitMix64 (Steele, Lea and Flood, OOPSLA 2014).  The n-th  */
@@ -616,6 +616,149 @@ static void seed_lbg(const uint32_t *keys, const uint32_t *w, int64_t n, int K, 
 }
 
 /* ------------------------------------------------------------------------- */
+/* WU: greedy orthogonal bipartitioning (Wu 1991), the preclustering method   */
+/* of Section 3.3 that initializes WSM-WU.  Colours fall in a 32 x 32 x 32     */
+/* grid of cells (5 bits per channel).  A box is a range of cells [lo, hi) on  */
+/* each axis.  Starting from the whole grid, the box with the largest weighted */
+/* variance (sum over its colours of w |x - mean|^2) is split by the           */
+/* axis-aligned cut between cells that minimizes the sum of the two halves'    */
+/* variances -- equivalently, maximizes |S_a|^2/W_a + |S_b|^2/W_b -- until K   */
+/* boxes exist or no box can be split.  The centres are the box means.         */
+/* Readings: the moments use the colours' full 8-bit values; ties go to the    */
+/* lower box index, to R before G before B and to the lower cut position; a    */
+/* cut must leave pixels on both sides; a box that cannot be cut gets variance */
+/* 0; when fewer than K boxes result, the remaining centres copy the last      */
+/* box's mean.  FP64 evaluation order: term(m) = ((Sr*Sr + Sg*Sg) + Sb*Sb)/W   */
+/* with every operation rounded, criterion = term(a) + term(b), variance =     */
+/* Q - term(m).  Box moments here are plain sums over the box's cells.         */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    int lo[3], hi[3];
+} wu_box;
+
+typedef struct {
+    int64_t w, s[3], q;
+} wu_mom;
+
+static int wu_cell(uint32_t key)
+{
+    return (int)(((key >> 19) & 31u) * 1024u + ((key >> 11) & 31u) * 32u + ((key >> 3) & 31u));
+}
+
+static void wu_add(wu_mom *a, const wu_mom *b)
+{
+    a->w += b->w;
+    a->q += b->q;
+    for (int ch = 0; ch < 3; ++ch) a->s[ch] += b->s[ch];
+}
+
+static void wu_sub(wu_mom *out, const wu_mom *a, const wu_mom *b)
+{
+    out->w = a->w - b->w;
+    out->q = a->q - b->q;
+    for (int ch = 0; ch < 3; ++ch) out->s[ch] = a->s[ch] - b->s[ch];
+}
+
+static void wu_moments(const wu_mom *cell, const wu_box *b, wu_mom *m)
+{
+    memset(m, 0, sizeof(*m));
+    for (int r = b->lo[0]; r < b->hi[0]; ++r)
+        for (int g = b->lo[1]; g < b->hi[1]; ++g)
+            for (int bb = b->lo[2]; bb < b->hi[2]; ++bb) wu_add(m, &cell[r * 1024 + g * 32 + bb]);
+}
+
+static double wu_term(const wu_mom *m)
+{
+    const double sr = (double)m->s[0], sg = (double)m->s[1], sb = (double)m->s[2];
+    return ((sr * sr + sg * sg) + sb * sb) / (double)m->w;
+}
+
+static double wu_variance(const wu_mom *cell, const wu_box *b)
+{
+    const int vol = (b->hi[0] - b->lo[0]) * (b->hi[1] - b->lo[1]) * (b->hi[2] - b->lo[2]);
+    if (vol <= 1) return 0.0;
+    wu_mom m;
+    wu_moments(cell, b, &m);
+    if (m.w == 0) return 0.0;
+    return (double)m.q - wu_term(&m);
+}
+
+OR_API int or_wu(const uint32_t *keys, const uint32_t *w, int64_t n, int K, double *c)
+{
+    if (n <= 0 || K <= 0) return -1;
+    wu_mom *cell = (wu_mom *)calloc(32768, sizeof(wu_mom));
+    wu_box *box = (wu_box *)malloc((size_t)K * sizeof(wu_box));
+    double *vv = (double *)malloc((size_t)K * sizeof(double));
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t r, g, b;
+        key_rgb(keys[i], &r, &g, &b);
+        wu_mom *m = &cell[wu_cell(keys[i])];
+        m->w += w[i];
+        m->s[0] += (int64_t)w[i] * r;
+        m->s[1] += (int64_t)w[i] * g;
+        m->s[2] += (int64_t)w[i] * b;
+        m->q += (int64_t)w[i] * (r * r + g * g + b * b);
+    }
+    for (int ax = 0; ax < 3; ++ax) {
+        box[0].lo[ax] = 0;
+        box[0].hi[ax] = 32;
+    }
+    vv[0] = wu_variance(cell, &box[0]);
+    int nb = 1, next = 0;
+    while (nb < K && vv[next] > 0.0) {
+        wu_mom whole;
+        wu_moments(cell, &box[next], &whole);
+        double best = -1.0;
+        int bax = -1, bpos = -1;
+        for (int ax = 0; ax < 3; ++ax) {
+            wu_mom half;
+            memset(&half, 0, sizeof(half));
+            for (int p = box[next].lo[ax] + 1; p < box[next].hi[ax]; ++p) {
+                /* half = the box's cells with coordinate < p on this axis */
+                wu_box slab = box[next];
+                slab.lo[ax] = p - 1;
+                slab.hi[ax] = p;
+                wu_mom plane;
+                wu_moments(cell, &slab, &plane);
+                wu_add(&half, &plane);
+                wu_mom rest;
+                wu_sub(&rest, &whole, &half);
+                if (half.w == 0 || rest.w == 0) continue;
+                const double f = wu_term(&half) + wu_term(&rest);
+                if (f > best) {
+                    best = f;
+                    bax = ax;
+                    bpos = p;
+                }
+            }
+        }
+        if (bax < 0) {
+            vv[next] = 0.0;
+        } else {
+            box[nb] = box[next];
+            box[nb].lo[bax] = bpos;
+            box[next].hi[bax] = bpos;
+            vv[next] = wu_variance(cell, &box[next]);
+            vv[nb] = wu_variance(cell, &box[nb]);
+            ++nb;
+        }
+        next = 0;
+        for (int k = 1; k < nb; ++k)
+            if (vv[k] > vv[next]) next = k;
+    }
+    for (int k = 0; k < nb; ++k) {
+        wu_mom m;
+        wu_moments(cell, &box[k], &m);
+        for (int ch = 0; ch < 3; ++ch) c[3 * k + ch] = (double)m.s[ch] / (double)m.w;
+    }
+    for (int k = nb; k < K; ++k) memcpy(c + 3 * k, c + 3 * (nb - 1), 3 * sizeof(double));
+    free(cell);
+    free(box);
+    free(vv);
+    return nb;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Entry point for seeding.  K_eff = min(K, N'); for K >= N' the centres are   */
 /* the unique colours in key order, padded with copies of the last one.        */
 /* Returns K_eff, or -1 for an unknown scheme.                                 */
@@ -637,6 +780,7 @@ OR_API int or_seed(const uint32_t *keys, const uint32_t *w, int64_t n, int K, in
     case OR_VAR: seed_var(keys, w, n, K, c); break;
     case OR_SFF: seed_sff(keys, n, K, seed, c); break;
     case OR_KPP: seed_kpp(keys, w, n, K, seed, c); break;
+    case OR_WU: or_wu(keys, w, n, K, c); break;
     default: return -1;
     }
     return K;

@@ -117,7 +117,7 @@ int kq_seed(const uint32_t *keys, const uint32_t *weights, const int32_t *n_uniq
     if (!ws_ok(ws, ws_bytes, &L)) return KQ_EINVAL;
     if (!keys || !weights || !n_unique || !centers) return KQ_EINVAL;
     if (K < 1 || K > kq::kMaxK) return KQ_EINVAL;
-    if (scheme < KQ_INIT_FGY || scheme > KQ_INIT_KPP) return KQ_EINVAL;
+    if ((scheme < KQ_INIT_FGY || scheme > KQ_INIT_KPP) && scheme != KQ_INIT_WU) return KQ_EINVAL;
     kq_seed_params p{1.0, 1e-4, 100, 0};
     if (params) {
         p = *params;

@@ -63,7 +63,8 @@ constexpr size_t kSoSsep = kSoSums + sizeof(unsigned long long) * 3 * kMaxK * 4;
 constexpr size_t kSoRows = kSoSsep + sizeof(float) * 2 * kMaxGrid;
 constexpr size_t kSoCent = kSoRows + sizeof(uint32_t) * kMaxK * kMaxK;
 constexpr size_t kSoChunk = kSoCent + sizeof(float4) * kMaxK;
-constexpr size_t kSoMisc = kSoChunk + sizeof(uint32_t) * kBatchChunks * 3 * 256;
+constexpr size_t kSoWu = kSoChunk + sizeof(uint32_t) * kBatchChunks * 3 * 256;
+constexpr size_t kSoMisc = kSoWu + kWuBytes;
 constexpr size_t kSlotBytes = (kSoMisc + sizeof(SlotMisc) + 4095) / 4096 * 4096;
 
 // Dynamic shared memory: one region reused by the steps in turn.
@@ -798,6 +799,22 @@ __device__ void group_seed(Group &g, const kq_batch_item &it, int64_t n, BatchSh
     case KQ_INIT_LBG:
         group_lbg(g, it, n, bs, sh, dyn, status);
         break;
+    case KQ_INIT_WU: {
+        __shared__ WuShared wsh;
+        unsigned long long *cell = g.at_slot<unsigned long long>(kSoWu);
+        unsigned long long *cum = cell + 5 * (size_t)kWuCells;
+        if (g.rank == 0)
+            for (int j = tid; j < 5 * kWuCells; j += kBT) cell[j] = 0ull;
+        g();
+        wu_accumulate(it.keys, it.weights, n, cell, g.gtid(), g.nthreads());
+        g();
+        if (g.rank == 0) {
+            wu_cumulate_block(cell, cum);
+            wu_split_block(cum, K, it.centers, wsh);
+        }
+        g();
+        break;
+    }
     default:
         break;
     }
@@ -868,7 +885,7 @@ __host__ __device__ __forceinline__ bool item_aligned(const kq_batch_item &it)
 __device__ __forceinline__ bool item_ok(const kq_batch_item &it)
 {
     return item_aligned(it) && it.n_pixels >= 0 && (it.rgb || it.n_pixels == 0) && (it.idx || it.n_pixels == 0) && it.K >= 1 &&
-           it.K <= kMaxK && it.scheme >= KQ_INIT_FGY && it.scheme <= KQ_INIT_USER && it.max_iter >= 1 &&
+           it.K <= kMaxK && it.scheme >= KQ_INIT_FGY && it.scheme <= KQ_INIT_WU && it.max_iter >= 1 &&
            it.capacity >= 0 && it.keys && it.weights && it.labels && it.scratch && it.centers && it.palette &&
            it.result && (it.scheme != KQ_INIT_LBG || it.lbg_max_iter >= 1);
 }
@@ -1015,7 +1032,7 @@ int grid_for(const BatchDev &d, int C) { return C > 1 ? d.clusters[C] * C : d.cl
 bool host_item_ok(const kq_batch_item &it)
 {
     return item_aligned(it) && it.n_pixels >= 0 && (it.rgb || it.n_pixels == 0) && (it.idx || it.n_pixels == 0) && it.K >= 1 &&
-           it.K <= kMaxK && it.scheme >= KQ_INIT_FGY && it.scheme <= KQ_INIT_USER && it.max_iter >= 1 &&
+           it.K <= kMaxK && it.scheme >= KQ_INIT_FGY && it.scheme <= KQ_INIT_WU && it.max_iter >= 1 &&
            it.capacity >= 0 && it.keys && it.weights && it.labels && it.scratch && it.centers && it.palette &&
            it.result && it.eps == it.eps && (it.scheme != KQ_INIT_LBG || it.lbg_max_iter >= 1);
 }

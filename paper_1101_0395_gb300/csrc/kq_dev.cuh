@@ -23,6 +23,9 @@ constexpr int kMaxGrid = 4096;             // upper bound on persistent grid siz
 constexpr int kSeedChunks = 512;           // chunks of the unique list for VAR / DEN lookups
 constexpr int kDenCells = 64;              // 4 levels per channel
 constexpr uint64_t kWaitNs = 4000000000ull;  // device-side wait limit (4 s)
+constexpr int kWuCells = 32 * 32 * 32;     // Wu's grid: 5 bits per channel
+constexpr int kWuCum = 33 * 33 * 33;       // cumulative moments with a zero border
+constexpr size_t kWuBytes = sizeof(unsigned long long) * 5 * ((size_t)kWuCells + kWuCum);
 
 // ---------------------------------------------------------------- control block
 // Lives at the start of the workspace.  Fields touched by spinning blocks sit on
@@ -49,7 +52,7 @@ static_assert(sizeof(Ctl) <= 4096, "control block must fit its region");
 struct Layout {
     size_t ctl, hist_cnt, hist_bits, hist_chunk, lut;
     size_t l_sums, l_sse, l_rows, l_cent;
-    size_t s_d2, s_part, s_slot, s_chunk, s_gcnt, s_misc, s_labels, s_centers;
+    size_t s_d2, s_part, s_slot, s_chunk, s_gcnt, s_misc, s_labels, s_centers, s_wu;
     size_t total;
     int64_t max_unique;
 };
@@ -82,6 +85,7 @@ __host__ __device__ inline Layout layout_for(int64_t max_unique)
     L.s_gcnt = take(sizeof(uint32_t) * 3 * 256 + sizeof(unsigned long long) * kDenCells * 2);
     L.s_misc = take(65536);
     L.s_centers = take(sizeof(double) * kMaxK * 3);
+    L.s_wu = take(kWuBytes);
     L.s_d2 = take(2 * sizeof(uint32_t) * (size_t)mu);
     L.s_labels = take((size_t)mu);
     L.total = o;

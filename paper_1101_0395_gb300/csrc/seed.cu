@@ -18,6 +18,9 @@
 //   DEN  per-chunk cell counts, the seat apportionment on one thread, then one
 //        block per cell draws and locates its members.
 //   LBG  centroid, then split rounds that call the Lloyd kernel.
+//   WU   (Section 3.3's preclustering, the WSM-WU initializer) moments per 32^3
+//        cell by atomics over the unique colours, then one block builds the
+//        cumulative moments and makes the greedy splits.
 #include <math.h>
 
 #include "seed_dev.cuh"
@@ -636,6 +639,25 @@ __global__ void seed_lbg_split(const int32_t *n_unique, int K, int m, double eps
     lbg_split(K, m, eps, cs, centers);
 }
 
+// ---------------------------------------------------------------- WU
+__global__ void seed_wu_acc(const uint32_t *keys, const uint32_t *w, const int32_t *n_unique, int K,
+                            unsigned long long *cell)
+{
+    const int64_t n = *n_unique;
+    if (n <= K) return;
+    wu_accumulate(keys, w, n, cell, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
+}
+
+__global__ void __launch_bounds__(1024) seed_wu_split(const int32_t *n_unique, int K, const unsigned long long *cell,
+                                                      unsigned long long *cum, double *centers)
+{
+    __shared__ WuShared sh;
+    const int64_t n = *n_unique;
+    if (n <= K) return;
+    wu_cumulate_block(cell, cum);
+    wu_split_block(cum, K, centers, sh);
+}
+
 constexpr size_t kClSmem = sizeof(uint32_t) * 4 * (size_t)kClPer;  // keys, weights, 2 x D^2
 
 // Largest cluster (16, else 8) of seed_far_cluster this device can run, or 0.
@@ -778,6 +800,16 @@ int launch_seed(const uint32_t *keys, const uint32_t *w, const int32_t *n_unique
         seed_chunk_counts<<<kSeedChunks, kChunkBlock, 0, s>>>(keys, w, n_unique, K, 1, chunk_cnt, gcnt, cellw, ctl);
         seed_den_quota<<<1, 32, 0, s>>>(n_unique, K, gcnt, cellw, quota);
         seed_den_pick<<<kDenCells, 256, 0, s>>>(keys, n_unique, K, seed, chunk_cnt, gcnt, quota, centers);
+        break;
+    }
+    case KQ_INIT_WU: {
+        unsigned long long *cell = at<unsigned long long>(ws, L.s_wu);
+        unsigned long long *cum = cell + 5 * (size_t)kWuCells;
+        if (cudaMemsetAsync(cell, 0, sizeof(unsigned long long) * 5 * (size_t)kWuCells, s) != cudaSuccess)
+            return KQ_ECUDA;
+        const DeviceInfo di = device_info();
+        seed_wu_acc<<<di.sms * 4, 256, 0, s>>>(keys, w, n_unique, K, cell);
+        seed_wu_split<<<1, 1024, 0, s>>>(n_unique, K, cell, cum, centers);
         break;
     }
     case KQ_INIT_LBG: {

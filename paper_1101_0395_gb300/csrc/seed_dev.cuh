@@ -339,5 +339,214 @@ __device__ void var_pick_warp(const uint32_t *keys, int64_t n, int K, int g, int
     if (lane == 0) key_to_centre(centers + 3 * g, keys[idx]);
 }
 
+
+// ---------------------------------------------------------------- WU (Section 3.3)
+// Wu's greedy orthogonal bipartitioning.  Five moment arrays (W, S_R, S_G, S_B and
+// Q = sum w |x|^2) over a 32^3 grid of cells, their 33^3 cumulative sums with a
+// zero border, and boxes [lo, hi) of cells whose moments are eight-corner
+// differences of the cumulative sums (exact in 64-bit integers).  The FP64
+// criterion and variance are evaluated with explicitly rounded operations in one
+// fixed order: term = ((S_R^2 + S_G^2) + S_B^2) / W, criterion = term(a) +
+// term(b), variance = Q - term; ties go to the lower box index, R before G before
+// B, and the lower cut position.
+struct WuMom {
+    unsigned long long w, s[3], q;
+};
+
+struct WuBox {
+    int8_t lo[3], hi[3];
+};
+
+__device__ __forceinline__ int wu_cell(uint32_t key)
+{
+    return (int)(((key >> 19) & 31u) * 1024u + ((key >> 11) & 31u) * 32u + ((key >> 3) & 31u));
+}
+
+__device__ __forceinline__ int wu_cidx(int r, int g, int b) { return (r * 33 + g) * 33 + b; }
+
+// Moments of the cells [lo, hi) of a box from the cumulative arrays cum[5][33^3].
+__device__ __forceinline__ WuMom wu_vol(const unsigned long long *cum, const int *lo, const int *hi)
+{
+    WuMom m;
+    unsigned long long v[5];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        const unsigned long long *c = cum + (size_t)j * kWuCum;
+        v[j] = __ldcg(c + wu_cidx(hi[0], hi[1], hi[2])) - __ldcg(c + wu_cidx(hi[0], hi[1], lo[2])) -
+               __ldcg(c + wu_cidx(hi[0], lo[1], hi[2])) + __ldcg(c + wu_cidx(hi[0], lo[1], lo[2])) -
+               __ldcg(c + wu_cidx(lo[0], hi[1], hi[2])) + __ldcg(c + wu_cidx(lo[0], hi[1], lo[2])) +
+               __ldcg(c + wu_cidx(lo[0], lo[1], hi[2])) - __ldcg(c + wu_cidx(lo[0], lo[1], lo[2]));
+    }
+    m.w = v[0];
+    m.s[0] = v[1];
+    m.s[1] = v[2];
+    m.s[2] = v[3];
+    m.q = v[4];
+    return m;
+}
+
+__device__ __forceinline__ double wu_term(const WuMom &m)
+{
+    const double sr = (double)m.s[0], sg = (double)m.s[1], sb = (double)m.s[2];
+    return __ddiv_rn(__dadd_rn(__dadd_rn(__dmul_rn(sr, sr), __dmul_rn(sg, sg)), __dmul_rn(sb, sb)), (double)m.w);
+}
+
+__device__ __forceinline__ double wu_variance(const unsigned long long *cum, const WuBox &b)
+{
+    int lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = b.lo[a];
+        hi[a] = b.hi[a];
+    }
+    const int vol = (hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2]);
+    if (vol <= 1) return 0.0;
+    const WuMom m = wu_vol(cum, lo, hi);
+    if (m.w == 0) return 0.0;
+    return __dsub_rn((double)m.q, wu_term(m));
+}
+
+// Adds each colour's moments to its cell (cell[5][32^3], zero on entry); threads
+// t of nt take colours t, t + nt, ...
+__device__ void wu_accumulate(const uint32_t *keys, const uint32_t *w, int64_t n, unsigned long long *cell, int64_t t,
+                              int64_t nt)
+{
+    for (int64_t i = t; i < n; i += nt) {
+        const uint32_t key = keys[i];
+        const unsigned long long wi = w[i];
+        const unsigned long long r = key_r(key), g = key_g(key), b = key_b(key);
+        const int c = wu_cell(key);
+        atomicAdd(cell + c, wi);
+        atomicAdd(cell + kWuCells + c, wi * r);
+        atomicAdd(cell + 2 * kWuCells + c, wi * g);
+        atomicAdd(cell + 3 * kWuCells + c, wi * b);
+        atomicAdd(cell + 4 * kWuCells + c, wi * (r * r + g * g + b * b));
+    }
+}
+
+// Cumulative sums cum[j][r][g][b] = sum of cell[j] over cells < (r, g, b) on every
+// axis, by one block (all its threads): prefix along B, then G, then R.
+__device__ void wu_cumulate_block(const unsigned long long *cell, unsigned long long *cum)
+{
+    const int nt = blockDim.x;
+    for (int l = threadIdx.x; l < 5 * 33 * 33; l += nt) {  // lines along B, border included
+        const int j = l / (33 * 33), rg = l % (33 * 33), r = rg / 33, g = rg % 33;
+        unsigned long long *c = cum + (size_t)j * kWuCum;
+        unsigned long long run = 0ull;
+        c[wu_cidx(r, g, 0)] = 0ull;
+        for (int b = 1; b <= 32; ++b) {
+            if (r > 0 && g > 0) run += cell[(size_t)j * kWuCells + (r - 1) * 1024 + (g - 1) * 32 + (b - 1)];
+            c[wu_cidx(r, g, b)] = run;
+        }
+    }
+    __syncthreads();
+    for (int l = threadIdx.x; l < 5 * 33 * 33; l += nt) {  // along G
+        const int j = l / (33 * 33), rb = l % (33 * 33), r = rb / 33, b = rb % 33;
+        unsigned long long *c = cum + (size_t)j * kWuCum;
+        unsigned long long run = 0ull;
+        for (int g = 1; g <= 32; ++g) {
+            run += c[wu_cidx(r, g, b)];
+            c[wu_cidx(r, g, b)] = run;
+        }
+    }
+    __syncthreads();
+    for (int l = threadIdx.x; l < 5 * 33 * 33; l += nt) {  // along R
+        const int j = l / (33 * 33), gb = l % (33 * 33), g = gb / 33, b = gb % 33;
+        unsigned long long *c = cum + (size_t)j * kWuCum;
+        unsigned long long run = 0ull;
+        for (int r = 1; r <= 32; ++r) {
+            run += c[wu_cidx(r, g, b)];
+            c[wu_cidx(r, g, b)] = run;
+        }
+    }
+    __syncthreads();
+}
+
+struct WuShared {
+    WuBox box[kMaxK];
+    double vv[kMaxK];
+    double f[96];
+    int nb, next, stop;
+};
+
+// The greedy splits and the box means, by one block of at least 96 threads.
+// Requires n > K (the K >= N' case is handled by the caller).
+__device__ void wu_split_block(const unsigned long long *cum, int K, double *centers, WuShared &sh)
+{
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        for (int a = 0; a < 3; ++a) {
+            sh.box[0].lo[a] = 0;
+            sh.box[0].hi[a] = 32;
+        }
+        sh.vv[0] = wu_variance(cum, sh.box[0]);
+        sh.nb = 1;
+        sh.next = 0;
+        sh.stop = !(sh.vv[0] > 0.0) || K <= 1;
+    }
+    __syncthreads();
+    while (!sh.stop) {
+        const int nx = sh.next;
+        if (tid < 96) {
+            const int ax = tid / 32, p = sh.box[nx].lo[ax] + 1 + tid % 32;
+            double f = -1.0;
+            if (p < sh.box[nx].hi[ax]) {
+                int lo[3], hi[3];
+                for (int a = 0; a < 3; ++a) {
+                    lo[a] = sh.box[nx].lo[a];
+                    hi[a] = sh.box[nx].hi[a];
+                }
+                const WuMom whole = wu_vol(cum, lo, hi);
+                hi[ax] = p;
+                const WuMom half = wu_vol(cum, lo, hi);
+                WuMom rest;
+                rest.w = whole.w - half.w;
+                for (int ch = 0; ch < 3; ++ch) rest.s[ch] = whole.s[ch] - half.s[ch];
+                rest.q = whole.q - half.q;
+                if (half.w != 0 && rest.w != 0) f = __dadd_rn(wu_term(half), wu_term(rest));
+            }
+            sh.f[tid] = f;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double best = -1.0;
+            int bt = -1;
+            for (int t = 0; t < 96; ++t)  // R, G, B; positions ascending; strict: first wins ties
+                if (sh.f[t] >= 0.0 && sh.f[t] > best) {
+                    best = sh.f[t];
+                    bt = t;
+                }
+            if (bt < 0) {
+                sh.vv[nx] = 0.0;
+            } else {
+                const int ax = bt / 32, p = sh.box[nx].lo[ax] + 1 + bt % 32;
+                const int nb = sh.nb;
+                sh.box[nb] = sh.box[nx];
+                sh.box[nb].lo[ax] = (int8_t)p;
+                sh.box[nx].hi[ax] = (int8_t)p;
+                sh.vv[nx] = wu_variance(cum, sh.box[nx]);
+                sh.vv[nb] = wu_variance(cum, sh.box[nb]);
+                sh.nb = nb + 1;
+            }
+            int nxt = 0;
+            for (int k = 1; k < sh.nb; ++k)
+                if (sh.vv[k] > sh.vv[nxt]) nxt = k;
+            sh.next = nxt;
+            sh.stop = sh.nb >= K || !(sh.vv[nxt] > 0.0);
+        }
+        __syncthreads();
+    }
+    const int nb = sh.nb;
+    for (int k = tid; k < K; k += blockDim.x) {
+        const int src = k < nb ? k : nb - 1;
+        int lo[3], hi[3];
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = sh.box[src].lo[a];
+            hi[a] = sh.box[src].hi[a];
+        }
+        const WuMom m = wu_vol(cum, lo, hi);
+        for (int ch = 0; ch < 3; ++ch) centers[3 * k + ch] = __ddiv_rn((double)m.s[ch], (double)m.w);
+    }
+}
+
 }  // namespace
 }  // namespace kq

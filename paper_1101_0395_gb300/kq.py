@@ -18,7 +18,7 @@ import torch
 from . import build as _build
 
 KQ_OK, KQ_EINVAL, KQ_ECAPACITY, KQ_ECUDA, KQ_ETIMEOUT, KQ_ENOMEM = 0, -1, -2, -3, -4, -5
-INIT = {"FGY": 0, "LBG": 1, "MMX": 2, "DEN": 3, "VAR": 4, "SFF": 5, "KPP": 6, "USER": 7}
+INIT = {"FGY": 0, "LBG": 1, "MMX": 2, "DEN": 3, "VAR": 4, "SFF": 5, "KPP": 6, "USER": 7, "WU": 8}
 LLOYD_LABELS_IN = 1
 LLOYD_DENSE = 2
 MAX_K = 256
@@ -215,7 +215,7 @@ def launches(call: str, n_pixels: int = 1, scheme: str = "KPP", K: int = 1) -> i
                 count += 2 + (1 if split < m else 0)
                 m += split
             return count
-        return {"FGY": 2, "MMX": 3, "KPP": 3, "SFF": 2, "VAR": 3, "DEN": 4}[scheme]
+        return {"FGY": 2, "MMX": 3, "KPP": 3, "SFF": 2, "VAR": 3, "DEN": 4, "WU": 3}[scheme]
     raise ValueError(call)
 
 

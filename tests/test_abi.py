@@ -50,6 +50,7 @@ def test_invalid_arguments_are_rejected_synchronously():
         assert L.kq_map(p, 10, p, p, p, p, K, p, None, WS, size, None) == kq.KQ_EINVAL
     assert L.kq_seed(p, p, p, 8, 7, 1, None, p, WS, size, None) == kq.KQ_EINVAL  # USER is not a seeding scheme
     assert L.kq_seed(p, p, p, 8, -1, 1, None, p, WS, size, None) == kq.KQ_EINVAL
+    assert L.kq_seed(p, p, p, 8, 9, 1, None, p, WS, size, None) == kq.KQ_EINVAL
     bad = kq.SeedParams(1.0, 1e-4, 0, 0)
     assert L.kq_seed(p, p, p, 8, 1, 1, C.byref(bad), p, WS, size, None) == kq.KQ_EINVAL
     assert L.kq_lloyd(p, p, p, 8, p, 1e-4, 0, 0, p, p, None, None, WS, size, None) == kq.KQ_EINVAL
@@ -93,7 +94,7 @@ def test_batch_planner_orders_largest_work_first():
     assert nb == 2 and list(order) == [3, 1, 0, 2]
     order, nb = kq.kq_batch_plan(items, kq.BatchConfig(4, 0, 6000))
     assert nb == 1 and list(order) == [3, 1, 0, 2]
-    for field, value in (("K", 0), ("K", 257), ("scheme", 8), ("max_iter", 0), ("n_pixels", -1),
+    for field, value in (("K", 0), ("K", 257), ("scheme", 9), ("max_iter", 0), ("n_pixels", -1),
                          ("capacity", -1), ("keys", 0), ("keys", (1 << 20) + 8), ("scratch", (1 << 20) + 16)):
         bad = items.copy()
         bad[1][field] = value

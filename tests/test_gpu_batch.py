@@ -26,7 +26,7 @@ CASES = [
     (96, 80, 16, "KPP"), (130, 70, 64, "MMX"), (40, 50, 8, "FGY"), (200, 150, 32, "VAR"),
     (120, 100, 24, "DEN"), (90, 90, 40, "SFF"), (64, 72, 12, "LBG"), (150, 220, 256, "KPP"),
     (70, 64, 1, "KPP"), (5, 4, 64, "KPP"), (0, 0, 8, "MMX"), (33, 17, 20, "USER"),
-    (260, 240, 128, "MMX"), (31, 29, 5, "VAR"), (48, 48, 200, "DEN"),
+    (260, 240, 128, "MMX"), (31, 29, 5, "VAR"), (48, 48, 200, "DEN"), (180, 200, 64, "WU"),
 ]
 
 

@@ -1,4 +1,5 @@
-"""kq_seed vs the oracle: every integer scheme bit-exact; LBG within tolerance."""
+"""kq_seed vs the oracle: every integer scheme and WU (integer moments, FP64 in one
+fixed order) bit-exact; LBG within tolerance."""
 import numpy as np
 import pytest
 
@@ -8,7 +9,7 @@ from tests.gpu_helpers import CENTER_ABS, Run, require_cuda
 
 pytestmark = pytest.mark.gpu
 
-EXACT = ["FGY", "MMX", "DEN", "VAR", "SFF", "KPP"]
+EXACT = ["FGY", "MMX", "DEN", "VAR", "SFF", "KPP", "WU"]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -68,3 +69,20 @@ def test_seed_lbg(plain, K):
     if K == 1:
         assert np.array_equal(got, want)  # the centroid: exact sums, one FP64 division
     assert np.max(np.abs(got - want)) <= CENTER_ABS
+
+
+def test_seed_wu_single_cell_and_large():
+    """All colours in one 8x8x8 cell: one box, every centre its mean.  And the
+    4096 x 4096 image (1.28 M colours) at K = 256."""
+    img = np.array([[8, 16, 0], [9, 16, 7], [8, 20, 3], [9, 20, 0]] * 5, dtype=np.uint8)
+    r = Run(img)
+    keys, w = r.histogram()
+    got = r.seed(3, "WU", 0)
+    want, _ = oracle.seed(keys, w, 3, "WU", 0)
+    assert np.array_equal(got, want) and np.all(got == got[0])
+    big = synth.WORKLOADS["large_4096"].make(0)
+    rb = Run(big)
+    kb, wb = rb.histogram()
+    got = rb.seed(256, "WU", 0)
+    want, _ = oracle.seed(kb, wb, 256, "WU", 0)
+    assert np.array_equal(got, want)

@@ -566,3 +566,119 @@ def test_seeds_are_data_points(small_image):
         assert all(int(k) in kset for k in ck)
         if scheme != "VAR":
             assert len(set(int(k) for k in ck)) == 16
+
+
+# ---------------------------------------------------------------- WU (Section 3.3)
+def _wu_cells(keys, w):
+    cells = {}
+    for k, wt in zip(keys.tolist(), w.tolist()):
+        r, g, b = k >> 16, (k >> 8) & 255, k & 255
+        c = (r >> 3, g >> 3, b >> 3)
+        m = cells.setdefault(c, [0, 0, 0, 0, 0])
+        m[0] += wt
+        m[1] += wt * r
+        m[2] += wt * g
+        m[3] += wt * b
+        m[4] += wt * (r * r + g * g + b * b)
+    return cells
+
+
+def _wu_box_mom(cells, lo, hi):
+    m = [0, 0, 0, 0, 0]
+    for c, v in cells.items():
+        if all(lo[a] <= c[a] < hi[a] for a in range(3)):
+            for j in range(5):
+                m[j] += v[j]
+    return m
+
+
+def _wu_exact(keys, w, K):
+    """Wu's greedy bipartitioning in exact rational arithmetic, written from the
+    method's statement: split the box of largest weighted variance by the cut
+    that minimizes the sum of the two halves' variances."""
+    from fractions import Fraction as F
+
+    cells = _wu_cells(keys, w)
+
+    def var(lo, hi):
+        vol = (hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2])
+        m = _wu_box_mom(cells, lo, hi)
+        if vol <= 1 or m[0] == 0:
+            return F(0)
+        return F(m[4]) - F(m[1] ** 2 + m[2] ** 2 + m[3] ** 2, m[0])
+
+    boxes = [([0, 0, 0], [32, 32, 32])]
+    vv = [var(*boxes[0])]
+    nxt = 0
+    while len(boxes) < K and vv[nxt] > 0:
+        lo, hi = boxes[nxt]
+        best, cut = None, None
+        for ax in range(3):
+            for p in range(lo[ax] + 1, hi[ax]):
+                h_hi = list(hi)
+                h_hi[ax] = p
+                r_lo = list(lo)
+                r_lo[ax] = p
+                ma, mb = _wu_box_mom(cells, lo, h_hi), _wu_box_mom(cells, r_lo, hi)
+                if ma[0] == 0 or mb[0] == 0:
+                    continue
+                tot = (F(ma[4]) - F(ma[1] ** 2 + ma[2] ** 2 + ma[3] ** 2, ma[0])) + \
+                      (F(mb[4]) - F(mb[1] ** 2 + mb[2] ** 2 + mb[3] ** 2, mb[0]))
+                if best is None or tot < best:
+                    best, cut = tot, (ax, p)
+        if cut is None:
+            vv[nxt] = F(0)
+        else:
+            ax, p = cut
+            h_hi = list(hi)
+            h_hi[ax] = p
+            r_lo = list(lo)
+            r_lo[ax] = p
+            boxes[nxt] = (lo, h_hi)
+            boxes.append((r_lo, hi))
+            vv[nxt] = var(lo, h_hi)
+            vv.append(var(r_lo, hi))
+        nxt = max(range(len(boxes)), key=lambda k: (vv[k], -k))
+    cen = []
+    for lo, hi in boxes:
+        m = _wu_box_mom(cells, lo, hi)
+        cen.append([m[1] / m[0], m[2] / m[0], m[3] / m[0]])
+    return np.array(cen), len(boxes)
+
+
+def test_wu_k1_is_the_weighted_mean():
+    rng = np.random.default_rng(41)
+    keys = np.unique(rng.integers(0, 1 << 24, 500, dtype=np.uint32))
+    w = rng.integers(1, 1000, keys.size).astype(np.uint32)
+    c, nb = oracle.wu(keys, w, 1)
+    assert nb == 1
+    W = int(w.astype(np.int64).sum())
+    for ch, sh in enumerate((16, 8, 0)):
+        s = int(((keys.astype(np.int64) >> sh) & 255).dot(w.astype(np.int64)))
+        assert c[0, ch] == s / W
+
+
+@pytest.mark.parametrize("seed", [3, 4, 5])
+def test_wu_matches_an_exact_rational_greedy(seed):
+    """Clustered random colours (a few cells), K = 2..7: the same boxes as exact
+    rational arithmetic, hence the same means."""
+    rng = np.random.default_rng(seed)
+    base = rng.integers(0, 256, (6, 3))
+    pts = (base[rng.integers(0, 6, 300)] + rng.integers(-20, 21, (300, 3))).clip(0, 255)
+    keys = np.unique(((pts[:, 0] << 16) | (pts[:, 1] << 8) | pts[:, 2]).astype(np.uint32))
+    w = rng.integers(1, 50, keys.size).astype(np.uint32)
+    for K in range(2, 8):
+        c, nb = oracle.wu(keys, w, K)
+        ce, nbe = _wu_exact(keys, w, K)
+        assert nb == nbe
+        assert np.array_equal(c[:nb], ce)
+
+
+def test_wu_cannot_split_a_single_cell():
+    # every colour in one 8 x 8 x 8 cell: one box, all centres its mean
+    keys = np.array([(r << 16) | (g << 8) | b for r in (8, 9) for g in (16, 20) for b in (0, 7)], dtype=np.uint32)
+    w = np.arange(1, keys.size + 1, dtype=np.uint32)
+    c, nb = oracle.wu(keys, w, 5)
+    assert nb == 1 and np.all(c == c[0])
+    c2, k_eff = oracle.seed(keys, w, 5, "WU", 0)
+    assert k_eff == 5 and np.array_equal(c, c2)
