@@ -434,7 +434,7 @@ def run_serving(args, rank, world, local) -> None:
     props = torch.cuda.get_device_properties(dev)
     clocks = ClockSampler("GPU-%s" % props.uuid if getattr(props, "uuid", None) else str(local))
     srv = serve.Server(serve.CudaBackend(cluster, split, device=dev, solo_max_pixels=max_px), pool_bytes, streams=2,
-                       max_wave=64)
+                       max_wave=64, solo_queue=8)
     srv.drain()
     for r in requests(8):
         srv.submit(r)
@@ -459,8 +459,8 @@ def run_serving(args, rank, world, local) -> None:
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "serving: Poisson arrivals at %g req/s for %g s; image side log-uniform 256-4096 "
                                    "(aspect 0.5-2, pool of 48 images), K uniform 8..256, %s seeds, eps=1e-4, "
-                                   "<=100 passes; memory-admitted continuous batching on 2 streams (a lone request on an idle "
-                                   "device runs on the whole GPU)"
+                                   "<=100 passes; memory-admitted continuous batching on 2 streams; while at most 8 requests "
+                                   "wait and no batch wave runs, requests go one at a time through the whole-GPU lane"
                                    % (args.rate, args.duration, SCHEME),
                        "requests": len(reqs), "launch_shape": {"cluster": cluster, "split_pixels": split},
                        "pool_bytes": pool_bytes, "l2": "inputs larger than L2 (no flush)"},

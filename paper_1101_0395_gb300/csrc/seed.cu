@@ -19,8 +19,8 @@
 //        block per cell draws and locates its members.
 //   LBG  centroid, then split rounds that call the Lloyd kernel.
 //   WU   (Section 3.3's preclustering, the WSM-WU initializer) moments per 32^3
-//        cell by atomics over the unique colours, then one block builds the
-//        cumulative moments and makes the greedy splits.
+//        cell by atomics over the unique colours, cumulative moments line by line
+//        over the grid, then one block makes the greedy splits.
 #include <math.h>
 
 #include "seed_dev.cuh"
@@ -648,13 +648,23 @@ __global__ void seed_wu_acc(const uint32_t *keys, const uint32_t *w, const int32
     wu_accumulate(keys, w, n, cell, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
 }
 
-__global__ void __launch_bounds__(1024) seed_wu_split(const int32_t *n_unique, int K, const unsigned long long *cell,
-                                                      unsigned long long *cum, double *centers)
+// Cumulative moments on the whole grid: step 0 copies the cells, steps 1-3 sum lines.
+__global__ void seed_wu_cum(const int32_t *n_unique, int K, const unsigned long long *cell, unsigned long long *cum,
+                            int step)
+{
+    const int64_t n = *n_unique;
+    if (n <= K) return;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (int64_t)gridDim.x * blockDim.x;
+    if (step == 0) wu_cum_copy(cell, cum, t, nt);
+    else wu_cum_lines(cum, step, t, nt);
+}
+
+__global__ void __launch_bounds__(1024) seed_wu_split(const int32_t *n_unique, int K, const unsigned long long *cum,
+                                                      double *centers)
 {
     __shared__ WuShared sh;
     const int64_t n = *n_unique;
     if (n <= K) return;
-    wu_cumulate_block(cell, cum);
     wu_split_block(cum, K, centers, sh);
 }
 
@@ -809,7 +819,10 @@ int launch_seed(const uint32_t *keys, const uint32_t *w, const int32_t *n_unique
             return KQ_ECUDA;
         const DeviceInfo di = device_info();
         seed_wu_acc<<<di.sms * 4, 256, 0, s>>>(keys, w, n_unique, K, cell);
-        seed_wu_split<<<1, 1024, 0, s>>>(n_unique, K, cell, cum, centers);
+        seed_wu_cum<<<(5 * kWuCum + 255) / 256, 256, 0, s>>>(n_unique, K, cell, cum, 0);
+        for (int step = 1; step <= 3; ++step)
+            seed_wu_cum<<<(5 * 33 * 33 + 127) / 128, 128, 0, s>>>(n_unique, K, cell, cum, step);
+        seed_wu_split<<<1, 1024, 0, s>>>(n_unique, K, cum, centers);
         break;
     }
     case KQ_INIT_LBG: {

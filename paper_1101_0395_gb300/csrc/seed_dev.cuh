@@ -147,10 +147,10 @@ __device__ void lbg_split(int K, int m, double eps, const unsigned long long *cs
             unsigned long long wa = 0;
             for (int k = 0; k < m; ++k) {
                 if (chosen[k]) continue;
-                const unsigned long long W = cs[5 * k + 3];
+                const unsigned long long W = __ldcg(cs + 5 * k + 3);
                 unsigned __int128 s2 = 0;
-                for (int ch = 0; ch < 3; ++ch) s2 += (unsigned __int128)cs[5 * k + ch] * cs[5 * k + ch];
-                const unsigned __int128 num = (unsigned __int128)W * cs[5 * k + 4] - s2;
+                for (int ch = 0; ch < 3; ++ch) s2 += (unsigned __int128)__ldcg(cs + 5 * k + ch) * __ldcg(cs + 5 * k + ch);
+                const unsigned __int128 num = (unsigned __int128)W * __ldcg(cs + 5 * k + 4) - s2;
                 if (arg < 0 || sse_greater(num, W, na, wa)) {
                     arg = k;
                     na = num;
@@ -343,8 +343,9 @@ __device__ void var_pick_warp(const uint32_t *keys, int64_t n, int K, int g, int
 // ---------------------------------------------------------------- WU (Section 3.3)
 // Wu's greedy orthogonal bipartitioning.  Five moment arrays (W, S_R, S_G, S_B and
 // Q = sum w |x|^2) over a 32^3 grid of cells, their 33^3 cumulative sums with a
-// zero border, and boxes [lo, hi) of cells whose moments are eight-corner
-// differences of the cumulative sums (exact in 64-bit integers).  The FP64
+// zero border (stored [grid point][moment]), and boxes [lo, hi) of cells whose
+// moments are eight-corner differences of the cumulative sums (exact in 64-bit
+// integers).  The FP64
 // criterion and variance are evaluated with explicitly rounded operations in one
 // fixed order: term = ((S_R^2 + S_G^2) + S_B^2) / W, criterion = term(a) +
 // term(b), variance = Q - term; ties go to the lower box index, R before G before
@@ -364,19 +365,25 @@ __device__ __forceinline__ int wu_cell(uint32_t key)
 
 __device__ __forceinline__ int wu_cidx(int r, int g, int b) { return (r * 33 + g) * 33 + b; }
 
-// Moments of the cells [lo, hi) of a box from the cumulative arrays cum[5][33^3].
+// Moments of the cells [lo, hi) of a box from the cumulative moments cum[33^3][5]
+// (the five moments of a grid point are adjacent).  Plain loads: the array is
+// read-only while boxes are cut, and the corners that candidate cuts share stay
+// in L1.
 __device__ __forceinline__ WuMom wu_vol(const unsigned long long *cum, const int *lo, const int *hi)
 {
     WuMom m;
     unsigned long long v[5];
+    const unsigned long long *c000 = cum + 5 * (size_t)wu_cidx(lo[0], lo[1], lo[2]);
+    const unsigned long long *c001 = cum + 5 * (size_t)wu_cidx(lo[0], lo[1], hi[2]);
+    const unsigned long long *c010 = cum + 5 * (size_t)wu_cidx(lo[0], hi[1], lo[2]);
+    const unsigned long long *c011 = cum + 5 * (size_t)wu_cidx(lo[0], hi[1], hi[2]);
+    const unsigned long long *c100 = cum + 5 * (size_t)wu_cidx(hi[0], lo[1], lo[2]);
+    const unsigned long long *c101 = cum + 5 * (size_t)wu_cidx(hi[0], lo[1], hi[2]);
+    const unsigned long long *c110 = cum + 5 * (size_t)wu_cidx(hi[0], hi[1], lo[2]);
+    const unsigned long long *c111 = cum + 5 * (size_t)wu_cidx(hi[0], hi[1], hi[2]);
 #pragma unroll
-    for (int j = 0; j < 5; ++j) {
-        const unsigned long long *c = cum + (size_t)j * kWuCum;
-        v[j] = __ldcg(c + wu_cidx(hi[0], hi[1], hi[2])) - __ldcg(c + wu_cidx(hi[0], hi[1], lo[2])) -
-               __ldcg(c + wu_cidx(hi[0], lo[1], hi[2])) + __ldcg(c + wu_cidx(hi[0], lo[1], lo[2])) -
-               __ldcg(c + wu_cidx(lo[0], hi[1], hi[2])) + __ldcg(c + wu_cidx(lo[0], hi[1], lo[2])) +
-               __ldcg(c + wu_cidx(lo[0], lo[1], hi[2])) - __ldcg(c + wu_cidx(lo[0], lo[1], lo[2]));
-    }
+    for (int j = 0; j < 5; ++j)
+        v[j] = c111[j] - c110[j] - c101[j] + c100[j] - c011[j] + c010[j] + c001[j] - c000[j];
     m.w = v[0];
     m.s[0] = v[1];
     m.s[1] = v[2];
@@ -424,60 +431,98 @@ __device__ void wu_accumulate(const uint32_t *keys, const uint32_t *w, int64_t n
 }
 
 // Cumulative sums cum[j][r][g][b] = sum of cell[j] over cells < (r, g, b) on every
-// axis, by one block (all its threads): prefix along B, then G, then R.
+// axis, with a zero border at index 0.  Step 0 copies the cells into the interior
+// and zeroes the border; steps 1-3 take prefix sums along B, G and R, one line of
+// 32 values per thread at a time (all 32 loaded before any is stored).  Threads t
+// of nt; between steps every thread must see the previous step's stores.
+__device__ __forceinline__ void wu_cum_copy(const unsigned long long *cell, unsigned long long *cum, int64_t t,
+                                            int64_t nt)
+{
+    for (int64_t e = t; e < 5 * (int64_t)kWuCum; e += nt) {
+        const int rgb = (int)(e / 5), j = (int)(e % 5);
+        const int r = rgb / (33 * 33), g = (rgb / 33) % 33, b = rgb % 33;
+        // the cells were filled by atomics (performed in L2): read them from L2
+        cum[e] = (r && g && b) ? __ldcg(cell + (size_t)j * kWuCells + (r - 1) * 1024 + (g - 1) * 32 + (b - 1)) : 0ull;
+    }
+}
+
+// step 1, 2, 3: lines along B, G, R
+__device__ __forceinline__ void wu_cum_lines(unsigned long long *cum, int step, int64_t t, int64_t nt)
+{
+    const int st = step == 1 ? 1 : (step == 2 ? 33 : 33 * 33);
+    for (int64_t l = t; l < 5 * 33 * 33; l += nt) {
+        const int j = (int)(l / (33 * 33)), u = (int)(l % (33 * 33)), x = u / 33, y = u % 33;
+        // the two coordinates other than the line's, each 0..32
+        const int base = step == 1 ? (x * 33 + y) * 33 : (step == 2 ? x * 33 * 33 + y : x * 33 + y);
+        unsigned long long *c = cum + 5 * (size_t)base + j;
+        unsigned long long carry = 0ull;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            unsigned long long v[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] = c[5 * (1 + 16 * h + i) * st];
+            v[0] += carry;
+#pragma unroll
+            for (int i = 1; i < 16; ++i) v[i] += v[i - 1];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) c[5 * (1 + 16 * h + i) * st] = v[i];
+            carry = v[15];
+        }
+    }
+}
+
+// All four steps by one block (all its threads).
 __device__ void wu_cumulate_block(const unsigned long long *cell, unsigned long long *cum)
 {
-    const int nt = blockDim.x;
-    for (int l = threadIdx.x; l < 5 * 33 * 33; l += nt) {  // lines along B, border included
-        const int j = l / (33 * 33), rg = l % (33 * 33), r = rg / 33, g = rg % 33;
-        unsigned long long *c = cum + (size_t)j * kWuCum;
-        unsigned long long run = 0ull;
-        c[wu_cidx(r, g, 0)] = 0ull;
-        for (int b = 1; b <= 32; ++b) {
-            if (r > 0 && g > 0) run += cell[(size_t)j * kWuCells + (r - 1) * 1024 + (g - 1) * 32 + (b - 1)];
-            c[wu_cidx(r, g, b)] = run;
-        }
-    }
+    wu_cum_copy(cell, cum, threadIdx.x, blockDim.x);
     __syncthreads();
-    for (int l = threadIdx.x; l < 5 * 33 * 33; l += nt) {  // along G
-        const int j = l / (33 * 33), rb = l % (33 * 33), r = rb / 33, b = rb % 33;
-        unsigned long long *c = cum + (size_t)j * kWuCum;
-        unsigned long long run = 0ull;
-        for (int g = 1; g <= 32; ++g) {
-            run += c[wu_cidx(r, g, b)];
-            c[wu_cidx(r, g, b)] = run;
-        }
+    for (int step = 1; step <= 3; ++step) {
+        wu_cum_lines(cum, step, threadIdx.x, blockDim.x);
+        __syncthreads();
     }
-    __syncthreads();
-    for (int l = threadIdx.x; l < 5 * 33 * 33; l += nt) {  // along R
-        const int j = l / (33 * 33), gb = l % (33 * 33), g = gb / 33, b = gb % 33;
-        unsigned long long *c = cum + (size_t)j * kWuCum;
-        unsigned long long run = 0ull;
-        for (int r = 1; r <= 32; ++r) {
-            run += c[wu_cidx(r, g, b)];
-            c[wu_cidx(r, g, b)] = run;
-        }
-    }
-    __syncthreads();
 }
 
 struct WuShared {
     WuBox box[kMaxK];
+    WuMom mom[kMaxK];   // moments of each box
+    WuMom half[96];     // each candidate cut's lower half
     double vv[kMaxK];
-    double f[96];
+    double f[96], vh[96], vr[96];
+    double wf[32];
+    int wi[32];
     int nb, next, stop;
 };
 
-// The greedy splits and the box means, by one block of at least 96 threads.
+// Largest v with the lowest index among ties, over the lanes of a warp; returns
+// (value, index) in every lane.  Lanes without a candidate pass index INT_MAX.
+__device__ __forceinline__ void wu_warp_argmax(double &v, int &i)
+{
+    for (int o = 16; o; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, i, o);
+        if (ov > v || (ov == v && oi < i)) {
+            v = ov;
+            i = oi;
+        }
+    }
+}
+
+// The greedy splits and the box means, by one block of 256 or more threads (a
+// multiple of 32).  Every candidate cut (axis, position) is evaluated by its own
+// thread, which also keeps the two halves' variances; the best cut and the next
+// box to split are warp-level argmaxes (largest value, lowest index), so the
+// choices are those of scanning candidates and boxes in order with a strict >.
 // Requires n > K (the K >= N' case is handled by the caller).
 __device__ void wu_split_block(const unsigned long long *cum, int K, double *centers, WuShared &sh)
 {
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) {
+        int lo[3] = {0, 0, 0}, hi[3] = {32, 32, 32};
         for (int a = 0; a < 3; ++a) {
             sh.box[0].lo[a] = 0;
             sh.box[0].hi[a] = 32;
         }
+        sh.mom[0] = wu_vol(cum, lo, hi);
         sh.vv[0] = wu_variance(cum, sh.box[0]);
         sh.nb = 1;
         sh.next = 0;
@@ -488,32 +533,50 @@ __device__ void wu_split_block(const unsigned long long *cum, int K, double *cen
         const int nx = sh.next;
         if (tid < 96) {
             const int ax = tid / 32, p = sh.box[nx].lo[ax] + 1 + tid % 32;
-            double f = -1.0;
+            double f = -1.0, vh = 0.0, vr = 0.0;
             if (p < sh.box[nx].hi[ax]) {
                 int lo[3], hi[3];
                 for (int a = 0; a < 3; ++a) {
                     lo[a] = sh.box[nx].lo[a];
                     hi[a] = sh.box[nx].hi[a];
                 }
-                const WuMom whole = wu_vol(cum, lo, hi);
+                const WuMom whole = sh.mom[nx];
+                const int full = hi[ax];
                 hi[ax] = p;
                 const WuMom half = wu_vol(cum, lo, hi);
+                sh.half[tid] = half;
                 WuMom rest;
                 rest.w = whole.w - half.w;
                 for (int ch = 0; ch < 3; ++ch) rest.s[ch] = whole.s[ch] - half.s[ch];
                 rest.q = whole.q - half.q;
-                if (half.w != 0 && rest.w != 0) f = __dadd_rn(wu_term(half), wu_term(rest));
+                if (half.w != 0 && rest.w != 0) {
+                    const double th = wu_term(half), tr = wu_term(rest);
+                    f = __dadd_rn(th, tr);
+                    // the halves' variances (0 for a single cell), as wu_variance gives them
+                    const int other = (hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2]) / (p - lo[ax]);
+                    vh = other * (p - lo[ax]) > 1 ? __dsub_rn((double)half.q, th) : 0.0;
+                    vr = other * (full - p) > 1 ? __dsub_rn((double)rest.q, tr) : 0.0;
+                }
             }
             sh.f[tid] = f;
+            sh.vh[tid] = vh;
+            sh.vr[tid] = vr;
+            double v = f;
+            int i = f >= 0.0 ? tid : 0x7fffffff;
+            wu_warp_argmax(v, i);
+            if (lane == 0) {
+                sh.wf[warp] = v;
+                sh.wi[warp] = i;
+            }
         }
         __syncthreads();
         if (tid == 0) {
             double best = -1.0;
             int bt = -1;
-            for (int t = 0; t < 96; ++t)  // R, G, B; positions ascending; strict: first wins ties
-                if (sh.f[t] >= 0.0 && sh.f[t] > best) {
-                    best = sh.f[t];
-                    bt = t;
+            for (int q = 0; q < 3; ++q)
+                if (sh.wi[q] != 0x7fffffff && sh.wf[q] > best) {
+                    best = sh.wf[q];
+                    bt = sh.wi[q];
                 }
             if (bt < 0) {
                 sh.vv[nx] = 0.0;
@@ -523,27 +586,48 @@ __device__ void wu_split_block(const unsigned long long *cum, int K, double *cen
                 sh.box[nb] = sh.box[nx];
                 sh.box[nb].lo[ax] = (int8_t)p;
                 sh.box[nx].hi[ax] = (int8_t)p;
-                sh.vv[nx] = wu_variance(cum, sh.box[nx]);
-                sh.vv[nb] = wu_variance(cum, sh.box[nb]);
+                const WuMom h = sh.half[bt], whole = sh.mom[nx];
+                WuMom rest;
+                rest.w = whole.w - h.w;
+                for (int ch = 0; ch < 3; ++ch) rest.s[ch] = whole.s[ch] - h.s[ch];
+                rest.q = whole.q - h.q;
+                sh.mom[nx] = h;
+                sh.mom[nb] = rest;
+                sh.vv[nx] = sh.vh[bt];
+                sh.vv[nb] = sh.vr[bt];
                 sh.nb = nb + 1;
             }
-            int nxt = 0;
-            for (int k = 1; k < sh.nb; ++k)
-                if (sh.vv[k] > sh.vv[nxt]) nxt = k;
-            sh.next = nxt;
-            sh.stop = sh.nb >= K || !(sh.vv[nxt] > 0.0);
+        }
+        __syncthreads();
+        // the next box: largest variance, lowest index
+        const int nb = sh.nb;
+        if (warp < (nb + 31) / 32) {
+            const int k = tid;
+            double v = k < nb ? sh.vv[k] : -1.0;
+            int i = k < nb ? k : 0x7fffffff;
+            wu_warp_argmax(v, i);
+            if (lane == 0) {
+                sh.wf[warp] = v;
+                sh.wi[warp] = i;
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double bv = sh.wf[0];
+            int bi = sh.wi[0];
+            for (int q = 1; q < (nb + 31) / 32; ++q)
+                if (sh.wf[q] > bv) {
+                    bv = sh.wf[q];
+                    bi = sh.wi[q];
+                }
+            sh.next = bi;
+            sh.stop = nb >= K || !(bv > 0.0);
         }
         __syncthreads();
     }
     const int nb = sh.nb;
     for (int k = tid; k < K; k += blockDim.x) {
-        const int src = k < nb ? k : nb - 1;
-        int lo[3], hi[3];
-        for (int a = 0; a < 3; ++a) {
-            lo[a] = sh.box[src].lo[a];
-            hi[a] = sh.box[src].hi[a];
-        }
-        const WuMom m = wu_vol(cum, lo, hi);
+        const WuMom m = sh.mom[k < nb ? k : nb - 1];
         for (int ch = 0; ch < 3; ++ch) centers[3 * k + ch] = __ddiv_rn((double)m.s[ch], (double)m.w);
     }
 }

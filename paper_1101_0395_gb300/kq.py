@@ -215,7 +215,7 @@ def launches(call: str, n_pixels: int = 1, scheme: str = "KPP", K: int = 1) -> i
                 count += 2 + (1 if split < m else 0)
                 m += split
             return count
-        return {"FGY": 2, "MMX": 3, "KPP": 3, "SFF": 2, "VAR": 3, "DEN": 4, "WU": 3}[scheme]
+        return {"FGY": 2, "MMX": 3, "KPP": 3, "SFF": 2, "VAR": 3, "DEN": 4, "WU": 7}[scheme]
     raise ValueError(call)
 
 

@@ -10,8 +10,11 @@ The server keeps on the device
   tables stay resident and zero between requests.
 
 ``step()`` is the scheduler.  It retires every wave whose completion event has
-fired (freeing its requests' blocks and its workspace), then, while a workspace
-is free and requests are waiting, forms a wave: requests are taken in arrival
+fired (freeing its requests' blocks and its workspace).  While few requests wait
+(``solo_queue``) and no batch wave runs, a backend with a whole-GPU lane serves
+them one at a time through the four single-image calls, the lowest latency
+under light load.  Otherwise, while a workspace is free and requests are
+waiting, it forms a wave: requests are taken in arrival
 order as long as their blocks fit in the pool (memory admission; the first that
 does not fit waits, so no request is overtaken), their pixels are copied in,
 and the wave runs as one kq_batch_run on its own stream, followed by the copies
@@ -127,8 +130,14 @@ class Wave:
 class Server:
     """Continuous-batching quantization server (see the module docstring)."""
 
-    def __init__(self, backend, pool_bytes: int, streams: int = 2, max_wave: int = 64, clock=time.perf_counter):
+    def __init__(self, backend, pool_bytes: int, streams: int = 2, max_wave: int = 64, clock=time.perf_counter,
+                 solo_queue: int = 2):
+        """solo_queue: with a backend that has a whole-GPU lane (launch_solo), requests
+        are served one at a time on it while at most this many wait and no batch wave
+        runs (the lowest latency under light load); longer queues form batch waves."""
         self.backend = backend
+        self.solo_queue = int(solo_queue)
+        self.solo_busy = False
         self.arena = Arena(pool_bytes)
         self.streams = int(streams)
         self.max_wave = int(max_wave)
@@ -166,10 +175,32 @@ class Server:
                     self.arena.release(r.block)
                     self.finished.append(r)
                 done += len(wv.requests)
-                self.free_slots.append(wv.slot)
+                if wv.slot < 0:
+                    self.solo_busy = False
+                else:
+                    self.free_slots.append(wv.slot)
             else:
                 still.append(wv)
         self.running = still
+        solo_lane = getattr(self.backend, "has_solo", False)
+        batch_running = any(wv.slot >= 0 for wv in self.running)
+        if solo_lane and self.waiting and len(self.waiting) <= self.solo_queue and not batch_running:
+            # short queue on a device without batch waves: the whole-GPU lane, one
+            # request at a time (a busy lane is waited for)
+            if self.solo_busy:
+                return done
+            r = self.waiting[0]
+            off = self.arena.alloc(r.nbytes)
+            if off is None:
+                return done
+            self.waiting.popleft()
+            r.block = off
+            r.admitted = self.now()
+            self.running.append(Wave(-1, [r], self.backend.launch_solo(r)))
+            self.solo_busy = True
+            self.waves += 1
+            self.max_running = max(self.max_running, len(self.running))
+            return done
         while self.free_slots and self.waiting:
             batch: List[Request] = []
             while self.waiting and len(batch) < self.max_wave:
@@ -184,7 +215,7 @@ class Server:
             if not batch:
                 break
             slot = self.free_slots.popleft()
-            handle = self.backend.launch(slot, batch, alone=not self.running)
+            handle = self.backend.launch(slot, batch)
             self.running.append(Wave(slot, batch, handle))
             self.waves += 1
             self.max_running = max(self.max_running, len(self.running))
@@ -245,9 +276,9 @@ class CudaBackend:
     OUT = ("idx", "palette", "centers", "result")
 
     def __init__(self, cluster: int = 1, split_pixels: int = 1 << 62, device=None, solo_max_pixels: int = 0):
-        """solo_max_pixels > 0: a wave of one request that finds the device idle runs
-        on the whole GPU through the four single-image calls (lowest latency under
-        light load) instead of one block group of kq_batch_run."""
+        """solo_max_pixels > 0 gives the server a whole-GPU lane (launch_solo) for
+        requests up to that many pixels: the four single-image calls on the whole
+        GPU, the lowest latency when few requests wait."""
         import torch
 
         from . import kq
@@ -290,13 +321,21 @@ class CudaBackend:
             t = self.torch.from_numpy(np.ascontiguousarray(t).reshape(-1))
         return t.reshape(-1)
 
-    def launch(self, slot: int, batch: List[Request], alone: bool = False):
+    @property
+    def has_solo(self) -> bool:
+        return self.solo is not None
+
+    def launch_solo(self, r: Request):
+        """One request on the whole GPU through the four single-image calls."""
+        if r.n_pixels > self.solo_max_pixels:
+            raise ValueError("request larger than the whole-GPU lane's buffers")
+        self.solo_waves += 1
+        self.h2d_bytes += 3 * r.n_pixels
+        self.d2h_bytes += r.n_pixels + 3 * r.K
+        return ("solo", self.solo.launch(0, [r]))
+
+    def launch(self, slot: int, batch: List[Request]):
         torch, kq = self.torch, self.kq
-        if self.solo is not None and alone and len(batch) == 1 and batch[0].n_pixels <= self.solo_max_pixels:
-            self.solo_waves += 1
-            self.h2d_bytes += 3 * batch[0].n_pixels
-            self.d2h_bytes += batch[0].n_pixels + 3 * batch[0].K
-            return ("solo", self.solo.launch(0, batch))
         s = self.streams[slot]
         base = self.pool.data_ptr()
         items = np.zeros(len(batch), dtype=kq.BATCH_ITEM_DTYPE)
@@ -392,7 +431,7 @@ class PlainBackend:
         # the Quantizers' workspaces were zero-filled on the current stream
         torch.cuda.current_stream(self.device).synchronize()
 
-    def launch(self, slot: int, batch: List[Request], alone: bool = False):
+    def launch(self, slot: int, batch: List[Request]):
         torch = self.torch
         s = self.streams[slot]
         q = self.q[slot]

@@ -20,7 +20,7 @@ class FakeBackend:
     def setup(self, pool_bytes, streams, max_wave):
         self.pool_bytes, self.n_streams, self.max_wave = pool_bytes, streams, max_wave
 
-    def launch(self, slot, batch, alone=False):
+    def launch(self, slot, batch):
         self.launched.append((slot, [r.rid for r in batch], self.server.arena.in_use))
         return {"polls": 0, "slot": slot}
 
@@ -133,3 +133,38 @@ def test_poisson_arrivals():
     assert np.all(np.diff(t) > 0) and t[-1] < 30.0
     assert abs(t.size - 6000) < 4 * np.sqrt(6000)
     assert np.array_equal(t, serve.poisson_arrivals(200.0, 30.0, 7))
+
+
+class FakeSoloBackend(FakeBackend):
+    has_solo = True
+
+    def __init__(self, delay=2):
+        super().__init__(delay)
+        self.solo = []
+
+    def launch_solo(self, r):
+        self.solo.append(r.rid)
+        return {"polls": 0, "slot": -1}
+
+
+def test_short_queues_use_the_whole_gpu_lane_and_long_ones_batch():
+    be = FakeSoloBackend(delay=2)
+    srv = serve.Server(be, 1 << 30, streams=2, max_wave=8, solo_queue=2)
+    be.server = srv
+    srv.submit(_req(0, 500))
+    srv.step()
+    assert be.solo == [0] and not be.launched          # one waiting, device idle: solo
+    srv.submit(_req(1, 500))
+    srv.step()
+    assert be.solo == [0] and not be.launched          # solo lane busy, short queue: wait for it
+    for i in range(2, 6):
+        srv.submit(_req(i, 500))
+    srv.step()
+    assert be.launched and be.launched[0][1] == [1, 2, 3, 4, 5]  # long queue: a batch wave
+    srv.submit(_req(6, 500))
+    srv.step()
+    assert 6 not in be.solo                            # a batch wave runs: short queues join batch lanes
+    assert be.launched[-1][1] == [6]
+    srv.drain()
+    assert sorted(r.rid for r in srv.finished) == list(range(7))
+    assert not srv.solo_busy
