@@ -16,6 +16,7 @@ constexpr uint32_t kPadEntry = 0x7F7FFF00u;
 // (row stride kRowCache + 1 words, so lanes reading different rows hit different banks).
 constexpr int kRowCache = 32;
 constexpr int kRowStride = kRowCache + 1;
+constexpr int kCoopLanes = 2;  // at most this many scanning lanes go to the warp-wide scan
 constexpr float kPruneSlack = 1.0f + 0x1p-17f;
 constexpr unsigned kFull = 0xffffffffu;
 
@@ -446,22 +447,43 @@ __device__ __forceinline__ void lloyd_body(const LloydArgs &a, LloydShared &sh, 
                 warp_accumulate(sh, narrow, act1, g1, w1, k1);
             }
         }
+        // The pruned loop does little arithmetic per colour, so the next chunk's key,
+        // weight and previous label are loaded before the current chunk is scanned:
+        // the memory latency overlaps the scan.
+        uint32_t nkey = 0u, nw = 0u;
+        int nlab = 0;
+        {
+            const int64_t c0 = b + (int64_t)G * warp, i0 = c0 * 32 + lane;
+            if (use_prev && c0 < nch && i0 < n) {
+                nkey = a.keys[i0];
+                nw = a.w[i0];
+                nlab = a.labels[i0];
+            }
+        }
         for (int64_t c = b + (int64_t)G * warp; use_prev && c < nch; c += (int64_t)G * kWarps) {
             const int64_t i = c * 32 + lane;
             const bool active = i < n;
-            uint32_t key = 0u, w = 0u;
+            uint32_t key = nkey, w = nw;
+            const int lab = nlab;
             int arg = 0;
             float best = 0.f;
-            if (active) {
-                key = a.keys[i];
-                w = a.w[i];
+            {
+                const int64_t c1 = c + (int64_t)G * kWarps, i1 = c1 * 32 + lane;
+                if (c1 < nch && i1 < n) {
+                    nkey = a.keys[i1];
+                    nw = a.w[i1];
+                    nlab = a.labels[i1];
+                }
             }
             if (use_prev) {
-                // Sort-means scan from the previous centre p.  Each lane first walks its own
-                // point's row through the shared-memory copy of the first kRowCache entries;
-                // points whose bound has not stopped them by then continue together, the
-                // whole warp testing 32 further entries of that point's row per step.
-                int p = active ? a.labels[i] : 0;
+                // Sort-means scan from the previous centre p.  Each lane walks its own
+                // point's row through the shared-memory copy of its first kRowCache
+                // entries while more than kCoopLanes lanes of the warp are still scanning;
+                // the points left then continue one at a time, the whole warp testing 32
+                // further entries of that point's row per step (shared memory up to
+                // kRowCache, then L2).  A few long scans thus cost a few warp steps instead
+                // of holding every lane of the warp.
+                int p = active ? lab : 0;
                 if (p >= K) p = 0;
                 const float x = (float)key_r(key), y = (float)key_g(key), z = (float)key_b(key);
                 const float4 cp = sh.c[p];
@@ -472,6 +494,7 @@ __device__ __forceinline__ void lloyd_body(const LloydArgs &a, LloydShared &sh, 
                 bool done = !active;
                 const uint32_t *rc = row_cache + p * kRowStride;
                 const int jl = Kp < kRowCache ? Kp : kRowCache;
+                int jstop = jl;
                 for (int j = 0; j < jl; ++j) {
                     if (!done) {
                         const uint32_t e = rc[j];
@@ -490,9 +513,15 @@ __device__ __forceinline__ void lloyd_body(const LloydArgs &a, LloydShared &sh, 
                             }
                         }
                     }
-                    if ((j & 7) == 7 && !__any_sync(kFull, !done)) break;
+                    if ((j & 3) == 3) {
+                        const unsigned left = __ballot_sync(kFull, !done);
+                        if (__popc(left) <= kCoopLanes) {
+                            jstop = j + 1;
+                            break;
+                        }
+                    }
                 }
-                unsigned tail = __ballot_sync(kFull, !done && Kp > kRowCache);
+                unsigned tail = __ballot_sync(kFull, !done && Kp > jstop);
                 while (tail) {
                     const int q = __ffs(tail) - 1;
                     tail &= tail - 1;
@@ -503,8 +532,11 @@ __device__ __forceinline__ void lloyd_body(const LloydArgs &a, LloydShared &sh, 
                     uint32_t qt = __shfl_sync(kFull, bt, q);
                     const float qx = (float)key_r(kq), qy = (float)key_g(kq), qz = (float)key_b(kq);
                     const uint32_t *row = a.rows + (size_t)pq * Kp;
-                    for (int j0 = kRowCache; j0 < Kp; j0 += 32) {
-                        const uint32_t e = (j0 + lane < Kp) ? __ldcg(row + j0 + lane) : kPadEntry;
+                    const uint32_t *rcq = row_cache + pq * kRowStride;
+                    for (int j0 = jstop; j0 < Kp; j0 += 32) {
+                        const int j = j0 + lane;
+                        uint32_t e = kPadEntry;
+                        if (j < Kp) e = j < kRowCache ? rcq[j] : __ldcg(row + j);
                         const bool brk = __uint_as_float(e & 0xFFFFFF00u) > thq;
                         const unsigned bal = __ballot_sync(kFull, brk);
                         const uint32_t t = e & 0xFFu;
