@@ -16,7 +16,8 @@ constexpr uint32_t kPadEntry = 0x7F7FFF00u;
 // (row stride kRowCache + 1 words, so lanes reading different rows hit different banks).
 constexpr int kRowCache = 32;
 constexpr int kRowStride = kRowCache + 1;
-constexpr int kCoopLanes = 2;  // at most this many scanning lanes go to the warp-wide scan
+constexpr int kCoopLanes = 2;
+constexpr int kDensePts = 2;  // points per lane in the full search  // at most this many scanning lanes go to the warp-wide scan
 constexpr float kPruneSlack = 1.0f + 0x1p-17f;
 constexpr unsigned kFull = 0xffffffffu;
 
@@ -221,69 +222,110 @@ __device__ __forceinline__ void dense_argmin(const LloydShared &sh, int K, float
     }
 }
 
-// dense_argmin for two points at once: each group of eight centres is loaded from
-// shared memory once (16-byte loads of the per-channel arrays) and used for both
-// points, which also gives the scheduler two independent chains.  Per point the
-// distances, the order of the comparisons and so the results are those of
-// dense_argmin.
-__device__ __forceinline__ void dense_argmin2(const LloydShared &sh, int K, float x0, float y0, float z0, float x1,
-                                              float y1, float z1, float &best0, int &arg0, float &best1, int &arg1)
+// Two FP32 values in one 64-bit register pair, for the packed f32x2 instructions.
+__device__ __forceinline__ unsigned long long pack2(float lo, float hi)
 {
-    best0 = best1 = __int_as_float(0x7f800000);
-    int bg0 = -1, bg1 = -1;
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+
+__device__ __forceinline__ void unpack2(unsigned long long v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
+// dist3 of one point (x, y, z broadcast into both halves of X, Y, Z) to two centres
+// (one per half of CX, CY, CZ) with the packed f32x2 subtract, multiply and fused
+// multiply-add.  Each half takes the same operations in the same order with the
+// same rounding as dist3, so each half equals dist3 bit for bit; one instruction
+// does the work of two, which halves the issue slots of the distance arithmetic.
+__device__ __forceinline__ unsigned long long dist3x2(unsigned long long X, unsigned long long Y,
+                                                      unsigned long long Z, unsigned long long CX,
+                                                      unsigned long long CY, unsigned long long CZ)
+{
+    unsigned long long dx, dy, dz, d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dx) : "l"(X), "l"(CX));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dy) : "l"(Y), "l"(CY));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dz) : "l"(Z), "l"(CZ));
+    asm("mul.rn.f32x2 %0, %1, %1;" : "=l"(d) : "l"(dx));
+    asm("fma.rn.f32x2 %0, %1, %1, %2;" : "=l"(d) : "l"(dy), "l"(d));
+    asm("fma.rn.f32x2 %0, %1, %1, %2;" : "=l"(d) : "l"(dz), "l"(d));
+    return d;
+}
+
+// Minimum of three values: one three-input min instruction.
+__device__ __forceinline__ float fmin3(float a, float b, float c)
+{
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+// dense_argmin for NP points at once: each group of eight centres is loaded from
+// shared memory once (16-byte loads of the per-channel arrays) and used for every
+// point, which also gives the scheduler NP independent chains.  Per point the
+// distances (dist3x2, equal to dist3), the order of the comparisons and so the
+// results are those of dense_argmin: the minimum of a group is exact whatever the
+// order it is taken in, and the first group holding the minimum is kept.
+template <int NP>
+__device__ __forceinline__ void dense_argmin_n(const LloydShared &sh, int K, const float (&x)[NP],
+                                               const float (&y)[NP], const float (&z)[NP], float (&best)[NP],
+                                               int (&arg)[NP])
+{
+    unsigned long long X[NP], Y[NP], Z[NP];
+    int bg[NP];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        best[q] = __int_as_float(0x7f800000);
+        bg[q] = -1;
+        X[q] = pack2(x[q], x[q]);
+        Y[q] = pack2(y[q], y[q]);
+        Z[q] = pack2(z[q], z[q]);
+    }
     int k0 = 0;
     for (; k0 + 8 <= K; k0 += 8) {
-        const float4 xa = *reinterpret_cast<const float4 *>(&sh.cx[k0]);
-        const float4 xb = *reinterpret_cast<const float4 *>(&sh.cx[k0 + 4]);
-        const float4 ya = *reinterpret_cast<const float4 *>(&sh.cy[k0]);
-        const float4 yb = *reinterpret_cast<const float4 *>(&sh.cy[k0 + 4]);
-        const float4 za = *reinterpret_cast<const float4 *>(&sh.cz[k0]);
-        const float4 zb = *reinterpret_cast<const float4 *>(&sh.cz[k0 + 4]);
-        const float cx[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
-        const float cy[8] = {ya.x, ya.y, ya.z, ya.w, yb.x, yb.y, yb.z, yb.w};
-        const float cz[8] = {za.x, za.y, za.z, za.w, zb.x, zb.y, zb.z, zb.w};
-        float d0[8], d1[8];
+        // centres k0 + 2h and k0 + 2h + 1 as one packed pair per channel
+        const ulonglong2 xa = *reinterpret_cast<const ulonglong2 *>(&sh.cx[k0]);
+        const ulonglong2 xb = *reinterpret_cast<const ulonglong2 *>(&sh.cx[k0 + 4]);
+        const ulonglong2 ya = *reinterpret_cast<const ulonglong2 *>(&sh.cy[k0]);
+        const ulonglong2 yb = *reinterpret_cast<const ulonglong2 *>(&sh.cy[k0 + 4]);
+        const ulonglong2 za = *reinterpret_cast<const ulonglong2 *>(&sh.cz[k0]);
+        const ulonglong2 zb = *reinterpret_cast<const ulonglong2 *>(&sh.cz[k0 + 4]);
+        const unsigned long long cx[4] = {xa.x, xa.y, xb.x, xb.y};
+        const unsigned long long cy[4] = {ya.x, ya.y, yb.x, yb.y};
+        const unsigned long long cz[4] = {za.x, za.y, zb.x, zb.y};
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            d0[j] = dist3(x0, y0, z0, cx[j], cy[j], cz[j]);
-            d1[j] = dist3(x1, y1, z1, cx[j], cy[j], cz[j]);
-        }
-        const float m0 =
-            fminf(fminf(fminf(d0[0], d0[1]), fminf(d0[2], d0[3])), fminf(fminf(d0[4], d0[5]), fminf(d0[6], d0[7])));
-        const float m1 =
-            fminf(fminf(fminf(d1[0], d1[1]), fminf(d1[2], d1[3])), fminf(fminf(d1[4], d1[5]), fminf(d1[6], d1[7])));
-        if (m0 < best0) {
-            best0 = m0;
-            bg0 = k0;
-        }
-        if (m1 < best1) {
-            best1 = m1;
-            bg1 = k0;
+        for (int q = 0; q < NP; ++q) {
+            float d[8];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) unpack2(dist3x2(X[q], Y[q], Z[q], cx[h], cy[h], cz[h]), d[2 * h], d[2 * h + 1]);
+            const float m = fmin3(fmin3(d[0], d[1], d[2]), fmin3(d[3], d[4], d[5]), fminf(d[6], d[7]));
+            if (m < best[q]) {
+                best[q] = m;
+                bg[q] = k0;
+            }
         }
     }
-    arg0 = 0;
-    arg1 = 0;
-    if (bg0 >= 0) {
 #pragma unroll
-        for (int j = 7; j >= 0; --j)
-            if (dist3(x0, y0, z0, sh.cx[bg0 + j], sh.cy[bg0 + j], sh.cz[bg0 + j]) == best0) arg0 = bg0 + j;
-    }
-    if (bg1 >= 0) {
+    for (int q = 0; q < NP; ++q) {
+        arg[q] = 0;
+        if (bg[q] >= 0) {
 #pragma unroll
-        for (int j = 7; j >= 0; --j)
-            if (dist3(x1, y1, z1, sh.cx[bg1 + j], sh.cy[bg1 + j], sh.cz[bg1 + j]) == best1) arg1 = bg1 + j;
+            for (int j = 7; j >= 0; --j)
+                if (dist3(x[q], y[q], z[q], sh.cx[bg[q] + j], sh.cy[bg[q] + j], sh.cz[bg[q] + j]) == best[q])
+                    arg[q] = bg[q] + j;
+        }
     }
     for (int k = k0; k < K; ++k) {
         const float cxk = sh.cx[k], cyk = sh.cy[k], czk = sh.cz[k];
-        const float e0 = dist3(x0, y0, z0, cxk, cyk, czk);
-        const float e1 = dist3(x1, y1, z1, cxk, cyk, czk);
-        if (e0 < best0) {
-            best0 = e0;
-            arg0 = k;
-        }
-        if (e1 < best1) {
-            best1 = e1;
-            arg1 = k;
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            const float e = dist3(x[q], y[q], z[q], cxk, cyk, czk);
+            if (e < best[q]) {
+                best[q] = e;
+                arg[q] = k;
+            }
         }
     }
 }
@@ -347,6 +389,42 @@ __device__ __forceinline__ void warp_accumulate(LloydShared &sh, bool narrow, bo
 // The Lloyd iteration run by G blocks (ranks b = 0..G-1) over n unique colours.
 // `sync` is a barrier across the G blocks that orders their global memory
 // accesses; it returns false when the wait gave up, and the blocks then return.
+// One step of the full search: chunks c, c + S, ..., c + (NP-1) S (all < the chunk
+// count), one point of each per lane; labels, SSE (in chunk order) and block sums.
+template <int NP>
+__device__ __forceinline__ void dense_step(const LloydArgs &a, LloydShared &sh, int K, int64_t n, int64_t c,
+                                           int64_t S, int lane, bool narrow, float &sse32, unsigned long long &ndc)
+{
+    uint32_t kk[NP], ww[NP];
+    float px[NP], py[NP], pz[NP], bd[NP];
+    int ga[NP];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        const int64_t iq = (c + q * S) * 32 + lane;
+        kk[q] = 0u;
+        ww[q] = 0u;
+        if (iq < n) {
+            kk[q] = a.keys[iq];
+            ww[q] = a.w[iq];
+        }
+        px[q] = (float)key_r(kk[q]);
+        py[q] = (float)key_g(kk[q]);
+        pz[q] = (float)key_b(kk[q]);
+    }
+    dense_argmin_n<NP>(sh, K, px, py, pz, bd, ga);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        const int64_t iq = (c + q * S) * 32 + lane;
+        const bool act = iq < n;
+        if (act) {
+            a.labels[iq] = (uint8_t)ga[q];
+            sse32 = __fadd_rn(sse32, __fmul_rn((float)ww[q], bd[q]));
+            ndc += (unsigned long long)K;
+        }
+        warp_accumulate(sh, narrow, act, ga[q], ww[q], kk[q]);
+    }
+}
+
 template <class Sync>
 __device__ __forceinline__ void lloyd_body(const LloydArgs &a, LloydShared &sh, uint32_t *row_cache, int64_t n, int b,
                                            int G, Sync &sync)
@@ -412,41 +490,15 @@ __device__ __forceinline__ void lloyd_body(const LloydArgs &a, LloydShared &sh, 
         __syncthreads();
         float sse32 = 0.f;
         unsigned long long ndc = 0ull;
-        // Full search (first pass, or no pruning): chunks c and c + S in one step, two
-        // points per lane.  The SSE is still added in chunk order, as in the pruned loop.
+        // Full search (first pass, or no pruning): chunks c, c + S, ..., c + (NP-1) S in
+        // one step, NP points per lane; a warp's last chunks, when fewer than NP are
+        // left, go one per step, so that no lane searches for a point it does not have.
+        // The SSE is still added in chunk order, as in the pruned loop.
         const int64_t S = (int64_t)G * kWarps;
-        for (int64_t c = b + (int64_t)G * warp; !use_prev && c < nch; c += 2 * S) {
-            const int64_t c1 = c + S;
-            const int64_t i0 = c * 32 + lane, i1 = c1 * 32 + lane;
-            const bool act0 = i0 < n, act1 = c1 < nch && i1 < n;
-            uint32_t k0 = 0u, w0 = 0u, k1 = 0u, w1 = 0u;
-            if (act0) {
-                k0 = a.keys[i0];
-                w0 = a.w[i0];
-            }
-            if (act1) {
-                k1 = a.keys[i1];
-                w1 = a.w[i1];
-            }
-            float b0, b1;
-            int g0, g1;
-            dense_argmin2(sh, K, (float)key_r(k0), (float)key_g(k0), (float)key_b(k0), (float)key_r(k1),
-                          (float)key_g(k1), (float)key_b(k1), b0, g0, b1, g1);
-            if (act0) {
-                a.labels[i0] = (uint8_t)g0;
-                sse32 = __fadd_rn(sse32, __fmul_rn((float)w0, b0));
-                ndc += (unsigned long long)K;
-            }
-            warp_accumulate(sh, narrow, act0, g0, w0, k0);
-            if (c1 < nch) {
-                if (act1) {
-                    a.labels[i1] = (uint8_t)g1;
-                    sse32 = __fadd_rn(sse32, __fmul_rn((float)w1, b1));
-                    ndc += (unsigned long long)K;
-                }
-                warp_accumulate(sh, narrow, act1, g1, w1, k1);
-            }
-        }
+        int64_t c = b + (int64_t)G * warp;
+        for (; !use_prev && c + (kDensePts - 1) * S < nch; c += kDensePts * S)
+            dense_step<kDensePts>(a, sh, K, n, c, S, lane, narrow, sse32, ndc);
+        for (; !use_prev && c < nch; c += S) dense_step<1>(a, sh, K, n, c, S, lane, narrow, sse32, ndc);
         // The pruned loop does little arithmetic per colour, so the next chunk's key,
         // weight and previous label are loaded before the current chunk is scanned:
         // the memory latency overlaps the scan.
