@@ -781,6 +781,54 @@ def run_gpu(args, rank, world, local) -> None:
                 "frac": achieved / hbm_peak, "traffic": None, "peak_source": "MEASURED_PEAKS hbm_gbs",
                 "algorithmic": "pixels 3 B in (+1 B out) + 8 B per unique colour"}
 
+    # ---- the other kernels against their own rooflines (after the timed region)
+    def ev_ms(fn, reps=10):
+        ts = []
+        for r in range(reps + 3):
+            flush.fill_(r & 255)
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            fn()
+            t1.record(stream)
+            torch.cuda.synchronize()
+            if r >= 3:
+                ts.append(t0.elapsed_time(t1))
+        return float(np.median(ts))
+
+    c_seed = q.centers[:3 * K]
+    kq.kq_seed(q.keys, q.weights, q.n_unique, K, SCHEME, SEED, c_seed, q.ws, conv_eps=wl.eps, max_iter=wl.max_iter)
+    c0 = c_seed.clone()
+
+    def dense(P):
+        def f():
+            c_seed.copy_(c0)
+            kq.kq_lloyd(q.keys, q.weights, q.n_unique, K, c_seed, -1.0, P, q.labels, q.palette[:3 * K], q.ws,
+                        stats=q.stats, flags=kq.LLOYD_DENSE)
+        return f
+
+    d1, d5 = ev_ms(dense(1)), ev_ms(dense(5))
+    pass_flop = float(FLOP_PER_DIST) * n_unique * K
+    marg = (d5 - d1) / 4.0
+    hist_b, map_b = 3.0 * n + 8.0 * n_unique, 4.0 * n + 8.0 * n_unique
+    kernels = {
+        "assignment_dense": {
+            "kernel": "lloyd_kernel with pruning off (full search of all K centres), K=%d, N'=%d" % (K, n_unique),
+            "bound": "fp32", "peak": fp32_peak, "unit": "TFLOP/s",
+            "one_pass_ms": d1, "five_pass_ms": d5, "marginal_pass_ms": marg,
+            "achieved_5_passes": 5 * pass_flop / (d5 * 1e-3) / 1e12,
+            "frac_5_passes": 5 * pass_flop / (d5 * 1e-3) / 1e12 / fp32_peak,
+            "achieved_marginal_pass": pass_flop / (marg * 1e-3) / 1e12 if marg > 0 else None,
+            "frac_marginal_pass": pass_flop / (marg * 1e-3) / 1e12 / fp32_peak if marg > 0 else None,
+            "algorithmic": "%d FLOP per distance x N' x K per pass; the marginal pass is (5 passes - 1 pass) / 4, "
+                           "which leaves out the launch and the one-time set-up" % FLOP_PER_DIST},
+        "histogram": {"bound": "hbm", "achieved": hist_b / (stage_mean[0] * 1e-3) / 1e9, "peak": hbm_peak,
+                      "unit": "GB/s", "frac": hist_b / (stage_mean[0] * 1e-3) / 1e9 / hbm_peak,
+                      "algorithmic": "3 B per pixel + 8 B per unique colour"},
+        "map": {"bound": "hbm", "achieved": map_b / (stage_mean[3] * 1e-3) / 1e9, "peak": hbm_peak,
+                "unit": "GB/s", "frac": map_b / (stage_mean[3] * 1e-3) / 1e9 / hbm_peak,
+                "algorithmic": "3 B in + 1 B out per pixel + 8 B per unique colour (palette table included)"},
+    }
+
     line = {"metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -793,6 +841,7 @@ def run_gpu(args, rank, world, local) -> None:
             "gdist_evals_per_s": {"actual": gdist_actual, "dense_equivalent": gdist_dense, "unit": "G/s",
                                   "ndc_per_colour_per_pass": st["ndc"] / max(1, n_unique * st["iters"])},
             "stages_ms": dict(zip(names, stage_mean)),
+            "kernels": kernels,
             "wall_s_timed_region": wall, "clock_samples": clk["samples"]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(img, K, wl.eps, wl.max_iter)

@@ -52,15 +52,19 @@ static_assert(sizeof(Ctl) <= 4096, "control block must fit its region");
 struct Layout {
     size_t ctl, hist_cnt, hist_bits, hist_chunk, lut;
     size_t l_sums, l_sse, l_rows, l_cent;
-    size_t s_d2, s_part, s_slot, s_chunk, s_gcnt, s_misc, s_labels, s_centers, s_wu;
+    size_t s_d2, s_part, s_slot, s_chunk, s_gcnt, s_misc, s_labels, s_centers, s_wu, s_gpart;
     size_t total;
     int64_t max_unique;
 };
 
 __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-// Fixed-size regions first, then the two that grow with the number of unique
-// colours (8 + 1 bytes per colour), so that the layout of a workspace can be
+// Entries per buffer of the seeding group sums: a sum per 32 colours of every block
+// slice, for any grid of up to kMaxGrid blocks (sum over blocks of ceil(slice / 32)).
+__host__ __device__ inline int64_t gpart_cap(int64_t max_unique) { return max_unique / 32 + 2 * (int64_t)kMaxGrid; }
+
+// Fixed-size regions first, then the three that grow with the number of unique
+// colours (8 + 1 + 0.5 bytes per colour), so that the layout of a workspace can be
 // recovered from its size alone.
 __host__ __device__ inline Layout layout_for(int64_t max_unique)
 {
@@ -88,6 +92,7 @@ __host__ __device__ inline Layout layout_for(int64_t max_unique)
     L.s_wu = take(kWuBytes);
     L.s_d2 = take(2 * sizeof(uint32_t) * (size_t)mu);
     L.s_labels = take((size_t)mu);
+    L.s_gpart = take(sizeof(unsigned long long) * 2 * (size_t)gpart_cap(mu));
     L.total = o;
     return L;
 }
@@ -101,7 +106,7 @@ inline Layout layout_from_bytes(size_t bytes)
         none.max_unique = 0;
         return none;
     }
-    int64_t mu = (int64_t)((bytes - base.s_d2) / 9);
+    int64_t mu = (int64_t)((bytes - base.s_d2) * 2 / 19);
     if (mu > kKeySpace) mu = kKeySpace;
     if (mu < 1) mu = 1;
     Layout L = layout_for(mu);

@@ -28,7 +28,7 @@
 namespace kq {
 namespace {
 
-constexpr int kFarBlock = 512;
+constexpr int kFarBlock = 1024;
 constexpr int kChunkBlock = 256;
 constexpr unsigned kFull = 0xffffffffu;
 
@@ -87,108 +87,129 @@ struct FarArgs {
     int64_t max_unique;
     double *centers;
     Ctl *ctl;
-    uint32_t *d2;              // [2][max_unique]
-    unsigned long long *part;  // [2][kMaxGrid]
-    unsigned long long *slot;  // [kMaxK]
-    int64_t cluster_cap;       // N' served by seed_far_cluster (0 when it is not used)
+    uint32_t *d2;               // [2][max_unique]
+    unsigned long long *part;   // [2][kMaxGrid] block sums
+    unsigned long long *gpart;  // [2][gpart_cap] sums of 32-colour groups
+    int64_t gpart_cap;
+    unsigned long long *slot;   // [kMaxK]
+    int64_t cluster_cap;        // N' served by seed_far_cluster (0 when it is not used)
 };
+
+constexpr int kFarWarps = kFarBlock / 32;
+constexpr int kFarChunk = 2048;  // fewest colours per block
+constexpr int kFarRes = 16384;  // colours a block keeps in shared memory (key, w, D^2)
+constexpr size_t kFarSmem = 3 * sizeof(uint32_t) * (size_t)kFarRes;
+constexpr int kFindRegs = 8;    // values per lane that warp_find keeps in registers
+constexpr int kFarUnroll = 2;   // groups per warp step in the D^2 update
 
 struct FarShared {
-    unsigned long long red[kFarBlock / 32];
-    unsigned long long scan[kFarBlock / 32];
-    unsigned long long resid;
-    int gstar;
+    unsigned long long wsum[kFarWarps];
     uint32_t key;
-    int found;
 };
 
-constexpr int kFarPer = 4;                    // consecutive colours per thread and chunk
-constexpr int kFarChunk = kFarBlock * kFarPer;
-
-// k-means++ sampling by inverse CDF.  With total = sum of the G block partials
-// and t = below(u, total), the sample is the first colour whose running sum of
-// P = w (first round) or w D^2 exceeds t.  Warp 0 finds the block from the
-// partials, then the block scans that block's slice one chunk at a time.
-// Every block computes the same key.
-__device__ uint32_t kpp_locate(const FarArgs &a, FarShared &sh, const unsigned long long *part,
-                               const uint32_t *d2, int G, int64_t n, uint64_t u, bool first_round)
+// First index i < count whose running sum of vals[0..i] exceeds t, and t minus the
+// sum before it (one warp; every lane returns the same).  Lane l sums the values
+// [l m, l m + m), m = ceil(count / 32), with one round of loads; a warp scan of the
+// lane sums finds the lane, which then walks its own values.  `draw`: t is
+// below(u, total of all values) instead of u itself.
+__device__ __forceinline__ int warp_find(const unsigned long long *vals, int count, bool draw, uint64_t u,
+                                         unsigned long long *resid)
 {
-    const int tid = threadIdx.x;
-    if (tid < 32) {
-        unsigned long long total = 0ull;
-        for (int g = tid; g < G; g += 32) total += __ldcg(part + g);
-        for (int o = 16; o; o >>= 1) total += __shfl_xor_sync(kFull, total, o);
-        const unsigned long long t = below(u, total);
-        unsigned long long run = 0ull, resid = 0ull;
-        int gstar = G - 1;
-        for (int base = 0; base < G; base += 32) {
-            const int g = base + tid;
-            const unsigned long long v = g < G ? __ldcg(part + g) : 0ull;
-            unsigned long long x = v;
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned long long y = __shfl_up_sync(kFull, x, o);
-                if (tid >= o) x += y;
-            }
-            const unsigned bal = __ballot_sync(kFull, g < G && run + x > t);
-            if (bal) {
-                const int l = __ffs(bal) - 1;
-                gstar = base + l;
-                resid = t - (run + __shfl_sync(kFull, x, l) - __shfl_sync(kFull, v, l));
-                break;
-            }
-            run += __shfl_sync(kFull, x, 31);
-        }
-        if (tid == 0) {
-            sh.gstar = gstar;
-            sh.resid = resid;
-            sh.found = 0;
-            sh.key = 0u;
-        }
+    const int lane = threadIdx.x & 31;
+    const int m = (count + 31) / 32;
+    unsigned long long v[kFindRegs];
+    unsigned long long ls = 0ull;
+#pragma unroll
+    for (int j = 0; j < kFindRegs; ++j) {
+        const int i = lane * m + j;
+        v[j] = (j < m && i < count) ? __ldcg(vals + i) : 0ull;
+        ls += v[j];
     }
-    __syncthreads();
-    const unsigned long long resid = sh.resid;
-    int64_t lo, hi;
-    slice_of(n, sh.gstar, G, &lo, &hi);
-    unsigned long long run = 0ull;
-    for (int64_t cb = lo; cb < hi; cb += kFarChunk) {
-        unsigned long long p[kFarPer];
-        uint32_t key[kFarPer];
-        unsigned long long tsum = 0ull;
+    for (int j = kFindRegs; j < m; ++j) {
+        const int i = lane * m + j;
+        if (i < count) ls += __ldcg(vals + i);
+    }
+    unsigned long long x = ls;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    const unsigned long long t = draw ? below(u, __shfl_sync(kFull, x, 31)) : u;
+    const int L = __ffs(__ballot_sync(kFull, x > t)) - 1;  // exists: t < total
+    unsigned long long run = x - ls;
+    int idx = 0;
+    if (lane == L) {
+        bool found = false;
 #pragma unroll
-        for (int k = 0; k < kFarPer; ++k) {
-            const int64_t i = cb + (int64_t)kFarPer * tid + k;
-            p[k] = 0ull;
-            key[k] = 0u;
-            if (i < hi) {
-                const unsigned long long wi = __ldcg(a.w + i);
-                p[k] = first_round ? wi : wi * (unsigned long long)__ldcg(d2 + i);
-                key[k] = __ldcg(a.keys + i);
-            }
-            tsum += p[k];
-        }
-        unsigned long long tot;
-        const unsigned long long ex = block_excl_scan_u64<kFarBlock>(tsum, sh.scan, &tot);
-        if (run + ex <= resid && resid < run + ex + tsum) {
-            unsigned long long acc = run + ex;
-#pragma unroll
-            for (int k = 0; k < kFarPer; ++k) {
-                if (acc <= resid && resid < acc + p[k]) {
-                    sh.key = key[k];
-                    sh.found = 1;
+        for (int j = 0; j < kFindRegs; ++j) {
+            if (!found && j < m) {
+                if (run + v[j] > t) {
+                    idx = lane * m + j;
+                    found = true;
+                } else {
+                    run += v[j];
                 }
-                acc += p[k];
             }
         }
-        __syncthreads();
-        if (sh.found) break;
-        run += tot;
+        for (int j = kFindRegs; !found && j < m; ++j) {
+            const unsigned long long vj = __ldcg(vals + lane * m + j);
+            if (run + vj > t) {
+                idx = lane * m + j;
+                found = true;
+            } else {
+                run += vj;
+            }
+        }
     }
-    return sh.key;  // a consistent total always finds a colour
+    idx = __shfl_sync(kFull, idx, L);
+    *resid = t - __shfl_sync(kFull, run, L);
+    return idx;
 }
 
+// k-means++ sampling by inverse CDF (warp 0 of every block, all computing the same
+// key).  With total = the sum of P over all colours (P = w in the first round, w D^2
+// after) and t = below(u, total), the sample is the first colour, in key order,
+// whose running sum of P exceeds t.  Three levels, one round of loads each: the
+// block sums, the 32-colour group sums of that block, the colours of that group.
+__device__ uint32_t far_locate(const FarArgs &a, int G, int64_t n, int64_t gstride, int buf, uint64_t u,
+                               bool first_round)
+{
+    const int lane = threadIdx.x & 31;
+    unsigned long long r1, r2;
+    const int g = warp_find(a.part + (size_t)buf * kMaxGrid, G, true, u, &r1);
+    int64_t lo, hi;
+    slice_of(n, g, G, &lo, &hi);
+    const int ng = (int)((hi - lo + 31) / 32);
+    const int q = warp_find(a.gpart + (size_t)buf * a.gpart_cap + (size_t)g * gstride, ng, false, r1, &r2);
+    const int64_t i = lo + 32 * (int64_t)q + lane;
+    unsigned long long p = 0ull;
+    uint32_t key = 0u;
+    if (i < hi) {
+        const unsigned long long wi = __ldcg(a.w + i);
+        p = first_round ? wi : wi * (unsigned long long)__ldcg(a.d2 + (size_t)buf * a.max_unique + i);
+        key = __ldcg(a.keys + i);
+    }
+    unsigned long long x = p;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    const int l3 = __ffs(__ballot_sync(kFull, x > r2)) - 1;
+    return __shfl_sync(kFull, key, l3 < 0 ? 0 : l3);
+}
+
+// KPP / minmax over the whole grid, for N' above what one cluster holds.  Block b
+// owns a contiguous slice of the unique colours; while a slice fits kFarRes colours
+// the block keeps its keys, weights and D^2 in shared memory for all K rounds (and,
+// for k-means++, also writes D^2 to global memory, where the other blocks read the
+// one group they sample from).  Warps take the slice's 32-colour groups in turn and
+// publish each group's sum of P (k-means++) or fold the packed (D^2, key) maximum
+// into the round's slot (minmax).  One grid barrier per round.
 __global__ void __launch_bounds__(kFarBlock, 1) seed_far(FarArgs a)
 {
     __shared__ FarShared sh;
+    extern __shared__ uint32_t far_smem[];  // key[kFarRes], w[kFarRes], d2[kFarRes]
+    uint32_t *s_key = far_smem, *s_w = far_smem + kFarRes, *s_d2 = far_smem + 2 * kFarRes;
     const int64_t n = *a.n_unique;
     if (n <= a.K || n <= a.cluster_cap) return;  // the cluster kernel serves N' <= cluster_cap
     const int K = a.K;
@@ -202,65 +223,117 @@ __global__ void __launch_bounds__(kFarBlock, 1) seed_far(FarArgs a)
         if (b == 0 && threadIdx.x == 0) fail(ctl, KQ_ENOMEM);
         return;
     }
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t per = (n + G - 1) / G;
+    const int64_t gstride = (per + 31) / 32;
+    const bool res = per <= kFarRes;  // the same for every block
     int64_t lo, hi;
     slice_of(n, b, G, &lo, &hi);
+    const int cnt = (int)(hi - lo);  // < 2^31: at most 2^24 colours in all
+    const int ng = (cnt + 31) / 32;
+    if (res) {
+        for (int64_t j = tid; j < cnt; j += kFarBlock) {
+            s_key[j] = a.keys[lo + j];
+            s_w[j] = a.w[lo + j];
+        }
+    }
     if (b == 0)
         for (int k = tid; k < kMaxK; k += kFarBlock) a.slot[k] = 0ull;
-    uint32_t ckey;
-    if (a.mode == 0) {
-        unsigned long long s = 0ull;
-        for (int64_t i = lo + tid; i < hi; i += kFarBlock) s += a.w[i];
-        s = block_sum_u64<kFarBlock>(s, sh.red);
-        if (tid == 0) a.part[b] = s;
-        if (!grid_sync(ctl, G, &bar_epoch)) return;
-        ckey = kpp_locate(a, sh, a.part, nullptr, G, n, rand64(a.seed, 2, 0), true);
-    } else {
-        if (!grid_sync(ctl, G, &bar_epoch)) return;  // the argmax slots are clear
-        ckey = __ldg(a.keys + below(rand64(a.seed, 3, 0), (uint64_t)n));
-    }
-    if (b == 0 && tid == 0) key_to_centre(a.centers, ckey);
-    for (int r = 1; r < K; ++r) {
-        // D^2 alternates between two buffers: other blocks may still be reading this
-        // round's values (to locate the sample) while this block starts the next round.
-        uint32_t *d2 = a.d2 + (size_t)(r & 1) * (size_t)a.max_unique;
-        const uint32_t *d2_prev = a.d2 + (size_t)((r - 1) & 1) * (size_t)a.max_unique;
-        unsigned long long acc = 0ull;
-        for (int64_t cb = lo; cb < hi; cb += kFarChunk) {
+    __syncthreads();
+    uint32_t ckey = 0u;
+    for (int r = 0; r < K; ++r) {
+        const int buf = r & 1;
+        if (r > 0 || a.mode == 0) {
+            // D^2 of round r alternates between two global buffers: other blocks may
+            // still read round r - 1's values while this block writes round r's.
+            uint32_t *d2 = a.d2 + (size_t)buf * (size_t)a.max_unique + lo;
+            const uint32_t *d2p = a.d2 + (size_t)(buf ^ 1) * (size_t)a.max_unique + lo;
+            unsigned long long *gp = a.gpart + (size_t)buf * a.gpart_cap + (size_t)b * gstride;
+            unsigned long long acc = 0ull;
+            const uint32_t *kp = a.keys + lo, *wp = a.w + lo;
+            // kFarUnroll groups per step (q0 + u kFarWarps): all loads first, then the
+            // arithmetic, the stores and the group sums
+            for (int q0 = warp; q0 < ng; q0 += kFarUnroll * kFarWarps) {
+                uint32_t key[kFarUnroll], wj[kFarUnroll], dp[kFarUnroll];
+                bool in[kFarUnroll];
 #pragma unroll
-            for (int k = 0; k < kFarPer; ++k) {
-                const int64_t i = cb + (int64_t)kFarPer * tid + k;
-                if (i < hi) {
-                    const uint32_t key = a.keys[i];
-                    const uint32_t d = key_dist2(key, ckey);
-                    const uint32_t md = (r == 1) ? d : min(d2_prev[i], d);
-                    d2[i] = md;
-                    if (a.mode == 0) {
-                        acc += (unsigned long long)a.w[i] * md;
-                    } else {
-                        const unsigned long long pk = mmx_pack(md, key);
-                        acc = pk > acc ? pk : acc;
+                for (int u = 0; u < kFarUnroll; ++u) {
+                    const int j = 32 * (q0 + u * kFarWarps) + lane;
+                    in[u] = q0 + u * kFarWarps < ng && j < cnt;
+                    key[u] = 0u;
+                    wj[u] = 0u;
+                    dp[u] = 0xFFFFFFFFu;
+                    if (in[u]) {
+                        key[u] = res ? s_key[j] : kp[j];
+                        wj[u] = res ? s_w[j] : wp[j];
+                        if (r >= 2) dp[u] = res ? s_d2[j] : __ldcg(d2p + j);
                     }
                 }
+                unsigned long long pv[kFarUnroll];
+#pragma unroll
+                for (int u = 0; u < kFarUnroll; ++u) {
+                    const int q = q0 + u * kFarWarps;
+                    const int j = 32 * q + lane;
+                    pv[u] = 0ull;
+                    if (r == 0) {
+                        pv[u] = wj[u];  // k-means++ first centre: probability w / sum w
+                    } else if (q < ng) {
+                        const uint32_t md = min(dp[u], key_dist2(key[u], ckey));
+                        if (in[u]) {
+                            if (res) s_d2[j] = md;
+                            // k-means++ reads the sampled group's D^2 from global memory
+                            if (!res || a.mode == 0) d2[j] = md;
+                        }
+                        if (in[u]) pv[u] = a.mode == 0 ? (unsigned long long)wj[u] * md : mmx_pack(md, key[u]);
+                    }
+                }
+                if (a.mode == 0) {
+                    // w D^2 < 2^32 * 3 * 255^2 < 2^50: the 25-bit halves of 32 such values
+                    // sum exactly in 32 bits, one warp reduction each
+#pragma unroll
+                    for (int u = 0; u < kFarUnroll; ++u) {
+                        const int q = q0 + u * kFarWarps;
+                        const uint32_t slo = __reduce_add_sync(kFull, (uint32_t)(pv[u] & 0x1FFFFFFull));
+                        const uint32_t shi = __reduce_add_sync(kFull, (uint32_t)(pv[u] >> 25));
+                        const unsigned long long gs = ((unsigned long long)shi << 25) + slo;
+                        if (q < ng) {
+                            if (lane == 0) gp[q] = gs;
+                            acc += gs;
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int u = 0; u < kFarUnroll; ++u) acc = pv[u] > acc ? pv[u] : acc;
+                }
             }
-        }
-        unsigned long long *part = a.part + (size_t)(r & 1) * kMaxGrid;
-        if (a.mode == 0) {
-            const unsigned long long s = block_sum_u64<kFarBlock>(acc, sh.red);
-            if (tid == 0) part[b] = s;
-        } else {
-            for (int o = 16; o; o >>= 1) {
-                const unsigned long long other = __shfl_xor_sync(kFull, acc, o);
-                acc = other > acc ? other : acc;
+            if (a.mode == 0) {
+                if (lane == 0) sh.wsum[warp] = acc;
+                __syncthreads();
+                if (tid == 0) {
+                    unsigned long long s = 0ull;
+                    for (int k = 0; k < kFarWarps; ++k) s += sh.wsum[k];
+                    a.part[(size_t)buf * kMaxGrid + b] = s;
+                }
+            } else {
+                for (int o = 16; o; o >>= 1) {
+                    const unsigned long long other = __shfl_xor_sync(kFull, acc, o);
+                    acc = other > acc ? other : acc;
+                }
+                if (lane == 0 && acc) atomicMax(a.slot + r, acc);
             }
-            if ((tid & 31) == 0 && acc) atomicMax(a.slot + r, acc);
         }
         if (!grid_sync(ctl, G, &bar_epoch)) return;
         if (a.mode == 0) {
-            ckey = kpp_locate(a, sh, part, d2, G, n, rand64(a.seed, 2, (uint32_t)r), false);
-        } else {
-            ckey = 0xFFFFFFu - (uint32_t)(__ldcg(a.slot + r) & 0xFFFFFFull);
+            if (warp == 0) {
+                const uint32_t k = far_locate(a, G, n, gstride, buf, rand64(a.seed, 2, (uint32_t)r), r == 0);
+                if (lane == 0) sh.key = k;
+            }
+        } else if (tid == 0) {
+            sh.key = r == 0 ? __ldg(a.keys + below(rand64(a.seed, 3, 0), (uint64_t)n))
+                            : 0xFFFFFFu - (uint32_t)(__ldcg(a.slot + r) & 0xFFFFFFull);
         }
+        __syncthreads();
+        ckey = sh.key;
         if (b == 0 && tid == 0) key_to_centre(a.centers + 3 * r, ckey);
     }
 }
@@ -771,7 +844,8 @@ int launch_seed(const uint32_t *keys, const uint32_t *w, const int32_t *n_unique
             cfg.numAttrs = 1;
             if (cudaLaunchKernelEx(&cfg, seed_far_cluster, ca) != cudaSuccess) return KQ_ECUDA;
         }
-        const int per_sm = max_coresident((const void *)seed_far, kFarBlock, 0);
+        if (set_smem(seed_far, kFarSmem)) return KQ_ECUDA;
+        const int per_sm = max_coresident((const void *)seed_far, kFarBlock, kFarSmem);
         if (per_sm < 1) return KQ_ECUDA;
         int grid = di.sms * per_sm;
         if (grid > kMaxGrid) grid = kMaxGrid;
@@ -787,11 +861,14 @@ int launch_seed(const uint32_t *keys, const uint32_t *w, const int32_t *n_unique
         a.ctl = ctl;
         a.d2 = at<uint32_t>(ws, L.s_d2);
         a.part = at<unsigned long long>(ws, L.s_part);
+        a.gpart = at<unsigned long long>(ws, L.s_gpart);
+        a.gpart_cap = gpart_cap(L.max_unique);
         a.slot = at<unsigned long long>(ws, L.s_slot);
         a.cluster_cap = (int64_t)ctas * kClPer;
         if (cudaMemsetAsync(&ctl->bar_count, 0, sizeof(uint32_t), s) != cudaSuccess) return KQ_ECUDA;
         void *args[] = {&a};
-        if (cudaLaunchCooperativeKernel((const void *)seed_far, dim3(grid), dim3(kFarBlock), args, 0, s) != cudaSuccess)
+        if (cudaLaunchCooperativeKernel((const void *)seed_far, dim3(grid), dim3(kFarBlock), args, kFarSmem, s) !=
+            cudaSuccess)
             return KQ_ECUDA;
         break;
     }

@@ -71,7 +71,39 @@ def test_seed_lbg(plain, K):
     assert np.max(np.abs(got - want)) <= CENTER_ABS
 
 
-def test_seed_wu_single_cell_and_large():
+@pytest.fixture(scope="module")
+def large():
+    img = synth.WORKLOADS["large_4096"].make(0)
+    r = Run(img)
+    keys, w = r.histogram()
+    return r, keys, w
+
+
+@pytest.mark.parametrize("scheme,K,seed", [("KPP", 256, 1), ("MMX", 256, 2), ("KPP", 7, 3), ("MMX", 2, 4)])
+def test_seed_exact_grid(large, scheme, K, seed):
+    """N' = 1.28 M, beyond one thread-block cluster: the whole-grid kernel, each
+    block holding its slice in shared memory."""
+    r, keys, w = large
+    assert len(keys) > 1_000_000
+    got = r.seed(K, scheme, seed)
+    want, _ = oracle.seed(keys, w, K, scheme, seed)
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("scheme", ["KPP", "MMX"])
+def test_seed_exact_grid_slices_in_global_memory(scheme):
+    """Uniform random 2048 x 2048 image, ~3.7 M unique colours: slices larger than a
+    block keeps in shared memory, so D^2 stays in global memory."""
+    img = np.random.default_rng(77).integers(0, 256, size=(2048, 2048, 3), dtype=np.uint8)
+    r = Run(img)
+    keys, w = r.histogram()
+    assert len(keys) > 3_000_000
+    got = r.seed(16, scheme, 5)
+    want, _ = oracle.seed(keys, w, 16, scheme, 5)
+    assert np.array_equal(got, want)
+
+
+def test_seed_wu_single_cell_and_large(large):
     """All colours in one 8x8x8 cell: one box, every centre its mean.  And the
     4096 x 4096 image (1.28 M colours) at K = 256."""
     img = np.array([[8, 16, 0], [9, 16, 7], [8, 20, 3], [9, 20, 0]] * 5, dtype=np.uint8)
@@ -80,9 +112,7 @@ def test_seed_wu_single_cell_and_large():
     got = r.seed(3, "WU", 0)
     want, _ = oracle.seed(keys, w, 3, "WU", 0)
     assert np.array_equal(got, want) and np.all(got == got[0])
-    big = synth.WORKLOADS["large_4096"].make(0)
-    rb = Run(big)
-    kb, wb = rb.histogram()
+    rb, kb, wb = large
     got = rb.seed(256, "WU", 0)
     want, _ = oracle.seed(kb, wb, 256, "WU", 0)
     assert np.array_equal(got, want)
