@@ -34,6 +34,7 @@ if ROOT not in sys.path:
 
 WORKLOAD = "paper_512"
 K_DEFAULT = 256
+SOLO_QUEUE = 8   # serving: waiting requests up to which the whole-GPU lane serves them one at a time
 SCHEME = "KPP"
 SEED = 1101
 FLOP_PER_DIST = 8          # 3 subtractions, 1 multiply, 2 fused multiply-adds
@@ -434,7 +435,7 @@ def run_serving(args, rank, world, local) -> None:
     props = torch.cuda.get_device_properties(dev)
     clocks = ClockSampler("GPU-%s" % props.uuid if getattr(props, "uuid", None) else str(local))
     srv = serve.Server(serve.CudaBackend(cluster, split, device=dev, solo_max_pixels=max_px), pool_bytes, streams=2,
-                       max_wave=64, solo_queue=8)
+                       max_wave=64, solo_queue=SOLO_QUEUE)
     srv.drain()
     for r in requests(8):
         srv.submit(r)
@@ -459,9 +460,9 @@ def run_serving(args, rank, world, local) -> None:
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "serving: Poisson arrivals at %g req/s for %g s; image side log-uniform 256-4096 "
                                    "(aspect 0.5-2, pool of 48 images), K uniform 8..256, %s seeds, eps=1e-4, "
-                                   "<=100 passes; memory-admitted continuous batching on 2 streams; while at most 8 requests "
+                                   "<=100 passes; memory-admitted continuous batching on 2 streams; while at most %d requests "
                                    "wait and no batch wave runs, requests go one at a time through the whole-GPU lane"
-                                   % (args.rate, args.duration, SCHEME),
+                                   % (args.rate, args.duration, SCHEME, SOLO_QUEUE),
                        "requests": len(reqs), "launch_shape": {"cluster": cluster, "split_pixels": split},
                        "pool_bytes": pool_bytes, "l2": "inputs larger than L2 (no flush)"},
             "clocks": {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},

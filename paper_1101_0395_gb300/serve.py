@@ -137,7 +137,7 @@ class Server:
         runs (the lowest latency under light load); longer queues form batch waves."""
         self.backend = backend
         self.solo_queue = int(solo_queue)
-        self.solo_busy = False
+        self.solo_inflight = 0
         self.arena = Arena(pool_bytes)
         self.streams = int(streams)
         self.max_wave = int(max_wave)
@@ -176,7 +176,7 @@ class Server:
                     self.finished.append(r)
                 done += len(wv.requests)
                 if wv.slot < 0:
-                    self.solo_busy = False
+                    self.solo_inflight -= 1
                 else:
                     self.free_slots.append(wv.slot)
             else:
@@ -185,9 +185,10 @@ class Server:
         solo_lane = getattr(self.backend, "has_solo", False)
         batch_running = any(wv.slot >= 0 for wv in self.running)
         if solo_lane and self.waiting and len(self.waiting) <= self.solo_queue and not batch_running:
-            # short queue on a device without batch waves: the whole-GPU lane, one
-            # request at a time (a busy lane is waited for)
-            if self.solo_busy:
+            # short queue on a device without batch waves: the whole-GPU lane, up to
+            # the backend's solo_slots requests in flight (so that one request's
+            # copies overlap another's kernels); a full lane is waited for
+            if self.solo_inflight >= getattr(self.backend, "solo_slots", 1):
                 return done
             r = self.waiting[0]
             off = self.arena.alloc(r.nbytes)
@@ -197,7 +198,7 @@ class Server:
             r.block = off
             r.admitted = self.now()
             self.running.append(Wave(-1, [r], self.backend.launch_solo(r)))
-            self.solo_busy = True
+            self.solo_inflight += 1
             self.waves += 1
             self.max_running = max(self.max_running, len(self.running))
             return done
@@ -288,6 +289,7 @@ class CudaBackend:
         self.cfg = kq.BatchConfig(int(cluster), 0, int(split_pixels))
         self.solo_max_pixels = int(solo_max_pixels)
         self.solo_waves = 0
+        self.solo_slots = 2
 
     def scratch_bytes(self, cap: int) -> int:
         return self.kq.kq_batch_scratch_bytes(cap)
@@ -310,7 +312,8 @@ class CudaBackend:
         self.solo = None
         if self.solo_max_pixels > 0:
             self.solo = PlainBackend(self.solo_max_pixels, device=self.device)
-            self.solo.setup(0, 1, 1)
+            self.solo.setup(0, self.solo_slots, 1)
+            self.solo_free = deque(range(self.solo_slots))
         # the workspaces were zero-filled on the current stream; the waves run on
         # their own streams
         torch.cuda.current_stream(self.device).synchronize()
@@ -332,7 +335,7 @@ class CudaBackend:
         self.solo_waves += 1
         self.h2d_bytes += 3 * r.n_pixels
         self.d2h_bytes += r.n_pixels + 3 * r.K
-        return ("solo", self.solo.launch(0, [r]))
+        return ("solo", self.solo.launch(self.solo_free.popleft(), [r]))
 
     def launch(self, slot: int, batch: List[Request]):
         torch, kq = self.torch, self.kq
@@ -391,6 +394,7 @@ class CudaBackend:
         kq = self.kq
         if handle[0] == "solo":
             self.solo.collect(handle[1], batch)
+            self.solo_free.append(handle[1][0])
             return
         stage = self.h_out[handle[0]].numpy()
         for r, o in zip(batch, handle[2]):

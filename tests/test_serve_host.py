@@ -137,6 +137,7 @@ def test_poisson_arrivals():
 
 class FakeSoloBackend(FakeBackend):
     has_solo = True
+    solo_slots = 1
 
     def __init__(self, delay=2):
         super().__init__(delay)
@@ -167,4 +168,20 @@ def test_short_queues_use_the_whole_gpu_lane_and_long_ones_batch():
     assert be.launched[-1][1] == [6]
     srv.drain()
     assert sorted(r.rid for r in srv.finished) == list(range(7))
-    assert not srv.solo_busy
+    assert srv.solo_inflight == 0
+
+
+def test_whole_gpu_lane_keeps_solo_slots_requests_in_flight():
+    be = FakeSoloBackend(delay=3)
+    be.solo_slots = 2
+    srv = serve.Server(be, 1 << 30, streams=2, max_wave=8, solo_queue=4)
+    be.server = srv
+    for i in range(3):
+        srv.submit(_req(i, 500))
+    srv.step()
+    srv.step()
+    assert be.solo == [0, 1] and not be.launched       # two in flight, the third waits for a slot
+    assert srv.solo_inflight == 2
+    srv.drain()
+    assert be.solo == [0, 1, 2] and srv.solo_inflight == 0
+    assert sorted(r.rid for r in srv.finished) == [0, 1, 2]
