@@ -70,7 +70,7 @@ constexpr size_t kSlotBytes = (kSoMisc + sizeof(SlotMisc) + 4095) / 4096 * 4096;
 // Dynamic shared memory: one region reused by the steps in turn.
 constexpr size_t kDynFgy = sizeof(uint32_t) * (2 * kMapSlots + kMaxK);
 constexpr size_t kDynSff = sizeof(uint32_t) * (2 * kMapSlots + 2 * kSffMax);
-constexpr size_t kDynRows = sizeof(uint32_t) * (size_t)kMaxK * kRowStride;
+constexpr size_t kDynRows = sizeof(uint32_t) * (size_t)kMaxK * kRowStride + sizeof(float) * kChunkSlots;
 constexpr size_t kDynBytes = kDynSff > kDynFgy ? (kDynSff > kDynRows ? kDynSff : kDynRows)
                                                : (kDynFgy > kDynRows ? kDynFgy : kDynRows);
 

@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(kLloydBlock, 1) lloyd_kernel(LloydArgs a)
 
 // Dynamic shared memory: the row cache for the largest K (one size for every
 // launch, so the occupancy query and the cooperative grid are the same for all K).
-size_t lloyd_smem_bytes() { return sizeof(uint32_t) * (size_t)kMaxK * kRowStride; }
+size_t lloyd_smem_bytes() { return sizeof(uint32_t) * (size_t)kMaxK * kRowStride + sizeof(float) * kChunkSlots; }
 
 int lloyd_smem_attr(size_t bytes)
 {

@@ -16,6 +16,8 @@ constexpr uint32_t kPadEntry = 0x7F7FFF00u;
 // (row stride kRowCache + 1 words, so lanes reading different rows hit different banks).
 constexpr int kRowCache = 32;
 constexpr int kRowStride = kRowCache + 1;
+constexpr int kChunkSlots = 4096;    // chunks per block up to which the pruned pass balances its warps
+constexpr int kChunkSlotsMin = 64;   // and from which
 constexpr int kCoopLanes = 2;
 constexpr int kDensePts = 2;  // points per lane in the full search  // at most this many scanning lanes go to the warp-wide scan
 constexpr float kPruneSlack = 1.0f + 0x1p-17f;
@@ -56,6 +58,7 @@ struct LloydShared {
     double sse_i;
     int conv;
     int narrow;
+    int next;  // next chunk slot of the balanced pruned schedule
 };
 
 // Ascending bitonic sort of the 32 * EPL values a warp holds, element e = lane * EPL
@@ -389,11 +392,21 @@ __device__ __forceinline__ void warp_accumulate(LloydShared &sh, bool narrow, bo
 // The Lloyd iteration run by G blocks (ranks b = 0..G-1) over n unique colours.
 // `sync` is a barrier across the G blocks that orders their global memory
 // accesses; it returns false when the wait gave up, and the blocks then return.
+// Sum of the 32 lanes' values in one fixed tree (the result in lane 0).
+__device__ __forceinline__ float chunk_sse(float v)
+{
+    for (int o = 16; o; o >>= 1) v = __fadd_rn(v, __shfl_down_sync(kFull, v, o));
+    return v;
+}
+
 // One step of the full search: chunks c, c + S, ..., c + (NP-1) S (all < the chunk
-// count), one point of each per lane; labels, SSE (in chunk order) and block sums.
+// count), one point of each per lane; labels, SSE and block sums.  The SSE goes to
+// the lane's running sum in chunk order, or (csse non-null) per chunk to csse[slot],
+// slot = (chunk - b) / G, the first chunk's slot being j0.
 template <int NP>
 __device__ __forceinline__ void dense_step(const LloydArgs &a, LloydShared &sh, int K, int64_t n, int64_t c,
-                                           int64_t S, int lane, bool narrow, float &sse32, unsigned long long &ndc)
+                                           int64_t S, int lane, bool narrow, float &sse32, unsigned long long &ndc,
+                                           float *csse, int j0)
 {
     uint32_t kk[NP], ww[NP];
     float px[NP], py[NP], pz[NP], bd[NP];
@@ -416,10 +429,15 @@ __device__ __forceinline__ void dense_step(const LloydArgs &a, LloydShared &sh, 
     for (int q = 0; q < NP; ++q) {
         const int64_t iq = (c + q * S) * 32 + lane;
         const bool act = iq < n;
+        const float e = act ? __fmul_rn((float)ww[q], bd[q]) : 0.f;
         if (act) {
             a.labels[iq] = (uint8_t)ga[q];
-            sse32 = __fadd_rn(sse32, __fmul_rn((float)ww[q], bd[q]));
+            if (!csse) sse32 = __fadd_rn(sse32, e);
             ndc += (unsigned long long)K;
+        }
+        if (csse) {
+            const float t = chunk_sse(e);
+            if (lane == 0) csse[j0 + q * kLloydBlock / 32] = t;
         }
         warp_accumulate(sh, narrow, act, ga[q], ww[q], kk[q]);
     }
@@ -436,6 +454,14 @@ __device__ __forceinline__ void lloyd_body(const LloydArgs &a, LloydShared &sh, 
     const bool prune = !(a.flags & KQ_LLOYD_DENSE);
     const bool labels_in = (a.flags & KQ_LLOYD_LABELS_IN) != 0;
     const int64_t nch = (n + 31) / 32;  // 32-colour chunks; this block takes b, b + G, ...
+    const int64_t nslot64 = nch > b ? (nch - 1 - b) / G + 1 : 0;  // this block's chunks
+    const int nslot = (int)(nslot64 < kChunkSlots ? nslot64 : kChunkSlots);
+    // the balanced schedule pays where a whole-grid launch gives a block many chunks
+    // (few: one chunk's atomic and reduction cost more than the waiting they save;
+    // the small groups of a batch measured slightly slower with it)
+    float *csse = G >= 32 && nslot64 >= kChunkSlotsMin && nslot64 <= kChunkSlots
+                      ? reinterpret_cast<float *>(row_cache + kMaxK * kRowStride)
+                      : nullptr;
 
     for (int k = tid; k < K; k += kLloydBlock) {
         const double x = a.centers[3 * k], y = a.centers[3 * k + 1], z = a.centers[3 * k + 2];
@@ -487,6 +513,7 @@ __device__ __forceinline__ void lloyd_body(const LloydArgs &a, LloydShared &sh, 
                 dst[3] = v.w;
             }
         }
+        if (tid == 0) sh.next = kWarps;
         __syncthreads();
         float sse32 = 0.f;
         unsigned long long ndc = 0ull;
@@ -497,13 +524,18 @@ __device__ __forceinline__ void lloyd_body(const LloydArgs &a, LloydShared &sh, 
         const int64_t S = (int64_t)G * kWarps;
         int64_t c = b + (int64_t)G * warp;
         for (; !use_prev && c + (kDensePts - 1) * S < nch; c += kDensePts * S)
-            dense_step<kDensePts>(a, sh, K, n, c, S, lane, narrow, sse32, ndc);
-        for (; !use_prev && c < nch; c += S) dense_step<1>(a, sh, K, n, c, S, lane, narrow, sse32, ndc);
+            dense_step<kDensePts>(a, sh, K, n, c, S, lane, narrow, sse32, ndc, csse, (int)((c - b) / G));
+        for (; !use_prev && c < nch; c += S)
+            dense_step<1>(a, sh, K, n, c, S, lane, narrow, sse32, ndc, csse, (int)((c - b) / G));
         // The pruned loop does little arithmetic per colour, so the next chunk's key,
         // weight and previous label are loaded before the current chunk is scanned:
         // the memory latency overlaps the scan.
+        // With csse (at most kChunkSlots chunks in this block) the warps take the
+        // block's chunks b + G j from a shared counter, so that a warp whose chunks
+        // scan long rows does not hold up the block; the SSE is then kept per chunk.
         uint32_t nkey = 0u, nw = 0u;
         int nlab = 0;
+        int jc = warp;
         {
             const int64_t c0 = b + (int64_t)G * warp, i0 = c0 * 32 + lane;
             if (use_prev && c0 < nch && i0 < n) {
@@ -512,16 +544,22 @@ __device__ __forceinline__ void lloyd_body(const LloydArgs &a, LloydShared &sh, 
                 nlab = a.labels[i0];
             }
         }
-        for (int64_t c = b + (int64_t)G * warp; use_prev && c < nch; c += (int64_t)G * kWarps) {
+        for (int64_t c = b + (int64_t)G * warp; use_prev && c < nch;) {
             const int64_t i = c * 32 + lane;
             const bool active = i < n;
             uint32_t key = nkey, w = nw;
             const int lab = nlab;
             int arg = 0;
             float best = 0.f;
+            int jn = jc + kWarps;
+            if (csse) {
+                if (lane == 0) jn = atomicAdd(&sh.next, 1);
+                jn = __shfl_sync(kFull, jn, 0);
+            }
+            const int64_t cn = b + (int64_t)G * jn;
             {
-                const int64_t c1 = c + (int64_t)G * kWarps, i1 = c1 * 32 + lane;
-                if (c1 < nch && i1 < n) {
+                const int64_t i1 = cn * 32 + lane;
+                if (cn < nch && i1 < n) {
                     nkey = a.keys[i1];
                     nw = a.w[i1];
                     nlab = a.labels[i1];
@@ -619,12 +657,25 @@ __device__ __forceinline__ void lloyd_body(const LloydArgs &a, LloydShared &sh, 
                 dense_argmin(sh, K, (float)key_r(key), (float)key_g(key), (float)key_b(key), best, arg);
                 ndc += (unsigned long long)K;
             }
+            const float e = active ? __fmul_rn((float)w, best) : 0.f;
             if (active) {
                 a.labels[i] = (uint8_t)arg;
-                // w < 2^32 and best are FP32; one rounding per product, FP64 above the thread
-                sse32 = __fadd_rn(sse32, __fmul_rn((float)w, best));
+                // w < 2^32 and best are FP32; one rounding per product, FP64 above the block
+                if (!csse) sse32 = __fadd_rn(sse32, e);
+            }
+            if (csse) {
+                const float t = chunk_sse(e);
+                if (lane == 0) csse[jc] = t;
             }
             warp_accumulate(sh, narrow, active, arg, w, key);
+            c = cn;
+            jc = jn;
+        }
+        if (csse) {
+            // the block's SSE: the chunks' sums in slot order, whoever computed them
+            __syncthreads();
+            sse32 = 0.f;
+            for (int jj = tid; jj < nslot; jj += kLloydBlock) sse32 = __fadd_rn(sse32, csse[jj]);
         }
         const float bsse = block_sum_f32<kLloydBlock>(sse32, sh.red_f);
         const unsigned long long bndc = block_sum_u64<kLloydBlock>(ndc, sh.red_u);
