@@ -16,10 +16,12 @@ constexpr uint32_t kPadEntry = 0x7F7FFF00u;
 // (row stride kRowCache + 1 words, so lanes reading different rows hit different banks).
 constexpr int kRowCache = 32;
 constexpr int kRowStride = kRowCache + 1;
-constexpr int kChunkSlots = 4096;    // chunks per block up to which the pruned pass balances its warps
-constexpr int kChunkSlotsMin = 64;   // and from which
-constexpr int kCoopLanes = 2;
-constexpr int kDensePts = 2;  // points per lane in the full search  // at most this many scanning lanes go to the warp-wide scan
+// A whole-grid launch whose blocks hold kChunkSlotsMin..kChunkSlots chunks balances
+// the pruned pass over the block's warps (a shared chunk counter).
+constexpr int kChunkSlots = 4096;
+constexpr int kChunkSlotsMin = 64;
+constexpr int kCoopLanes = 2;  // at most this many scanning lanes go to the warp-wide scan
+constexpr int kDensePts = 2;   // points per lane in the full search
 constexpr float kPruneSlack = 1.0f + 0x1p-17f;
 constexpr unsigned kFull = 0xffffffffu;
 
@@ -520,7 +522,8 @@ __device__ __forceinline__ void lloyd_body(const LloydArgs &a, LloydShared &sh, 
         // Full search (first pass, or no pruning): chunks c, c + S, ..., c + (NP-1) S in
         // one step, NP points per lane; a warp's last chunks, when fewer than NP are
         // left, go one per step, so that no lane searches for a point it does not have.
-        // The SSE is still added in chunk order, as in the pruned loop.
+        // The SSE is added as in the pruned loop: in chunk order per lane, or per chunk
+        // into csse.
         const int64_t S = (int64_t)G * kWarps;
         int64_t c = b + (int64_t)G * warp;
         for (; !use_prev && c + (kDensePts - 1) * S < nch; c += kDensePts * S)
@@ -530,7 +533,7 @@ __device__ __forceinline__ void lloyd_body(const LloydArgs &a, LloydShared &sh, 
         // The pruned loop does little arithmetic per colour, so the next chunk's key,
         // weight and previous label are loaded before the current chunk is scanned:
         // the memory latency overlaps the scan.
-        // With csse (at most kChunkSlots chunks in this block) the warps take the
+        // With csse (the balanced schedule, see kChunkSlots) the warps take the
         // block's chunks b + G j from a shared counter, so that a warp whose chunks
         // scan long rows does not hold up the block; the SSE is then kept per chunk.
         uint32_t nkey = 0u, nw = 0u;
