@@ -224,7 +224,9 @@ def test_empty_input():
 
 def test_large_image_lockstep():
     # 4096 x 4096 (16.7 Mpx, ~1.3M unique colours), K = 256: histogram bit-exact,
-    # seeds bit-exact, three lockstep passes
+    # seeds bit-exact, three lockstep passes; then the pruned and the full search
+    # (here with the balanced chunk schedule: ~260 chunks per block) give the same
+    # labels, centres and SSE history, bit for bit
     img = synth.WORKLOADS["large_4096"].make(0)
     r = Run(img)
     keys, w = r.histogram()
@@ -234,3 +236,9 @@ def test_large_image_lockstep():
     want, _ = oracle.seed(keys, w, 256, "KPP", 4096)
     assert np.array_equal(got, want)
     lockstep(r, keys, w, want, 3)
+    a = r.lloyd(want, eps=-1.0, max_iter=12)
+    b = r.lloyd(want, eps=-1.0, max_iter=12, flags=kq.LLOYD_DENSE)
+    assert np.array_equal(a["labels"], b["labels"])
+    assert np.array_equal(a["centers"], b["centers"])
+    assert np.array_equal(a["sse_hist"], b["sse_hist"])
+    assert a["stats"]["ndc"] < b["stats"]["ndc"] == 256 * keys.size * 12
