@@ -307,9 +307,10 @@ KQ_API int kq_batch_tune(const kq_batch_item *h_items, const kq_batch_item *item
  *  - Limit: K <= 256 (the array holds sums and rows for 256 centres); K > 256,
  *    like any invalid argument, returns KQ_EINVAL.
  *  - It allocates nothing: no cudaMalloc, no cudaFree, no allocating library call.
- *  - The first call on each device looks up the array's device address
- *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture.
+ *  - Every call looks up the array's device address in the current context
+ *    (cudaGetSymbolAddress, a host-side query); on a device that has not run
+ *    the library before, that first lookup loads its module, so make the first
+ *    call on each device before any stream capture.
  *  - Every call clears the control block (status, barrier counters) and uses
  *    the same array: calls that overlap on the GPU (several streams, several
  *    host threads on one device) race and give wrong results.  Order them.
@@ -332,10 +333,28 @@ KQ_API int kq_lloyd_noalloc(const uint32_t *keys, const uint32_t *weights, const
 KQ_API int kq_pixel_keys(const uint8_t *rgb, int64_t n_pixels, uint32_t *keys, uint32_t *weights, int32_t *n_out,
                          kq_stream_t stream);
 
+/*
+ * Failure detection.  Every device-side wait of the kernels that use `ws` (the
+ * grid barriers of kq_lloyd and of the whole-grid seeding, the exchanges of the
+ * cluster seeding) gives up after a time limit: it writes KQ_ETIMEOUT to the
+ * status word (and to kq_lloyd's stats), the other waiters follow, and the
+ * kernel returns, leaving the context usable.  This call sets, for the launches
+ * enqueued after it on `ws`:
+ *   wait_limit_us      the limit in microseconds (0: the default of 4 s);
+ *   missing_arrivals   arrivals every such wait expects beyond the blocks that
+ *                      take part -- 0 in normal use; a positive value makes the
+ *                      waits run out, which is how the timeout path is tested
+ *                      without faulting or hanging the GPU.
+ * Asynchronous on `stream`.  kq_status_clear() resets both to 0.
+ */
+KQ_API int kq_set_wait_limit(void *ws, size_t ws_bytes, uint32_t wait_limit_us, uint32_t missing_arrivals,
+                             kq_stream_t stream);
+
 /* Device status word of `ws` copied to *h_status (synchronizes `stream`). */
 KQ_API int kq_status_read(const void *ws, int32_t *h_status, kq_stream_t stream);
 
-/* Resets the device status word of `ws` to KQ_OK (asynchronous). */
+/* Resets the device status word of `ws` to KQ_OK, with the abort flag and the
+ * settings of kq_set_wait_limit (asynchronous). */
 KQ_API int kq_status_clear(void *ws, kq_stream_t stream);
 
 /* Static description of a status code. */

@@ -59,6 +59,12 @@ using kq::Layout;
 
 namespace {
 
+__global__ void set_wait_fields(kq::Ctl *ctl, uint32_t limit_us, uint32_t missing)
+{
+    ctl->wait_limit_us = limit_us;
+    ctl->missing = missing;
+}
+
 bool ws_ok(const void *ws, size_t ws_bytes, Layout *L)
 {
     if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u)) return false;
@@ -160,6 +166,15 @@ int kq_pixel_keys(const uint8_t *rgb, int64_t n_pixels, uint32_t *keys, uint32_t
     if (n_pixels > 0 && (!rgb || !keys)) return KQ_EINVAL;
     if (n_pixels == 0 && !n_out) return KQ_OK;
     return kq::launch_pixel_keys(rgb, n_pixels, keys, weights, n_out, (cudaStream_t)stream);
+}
+
+int kq_set_wait_limit(void *ws, size_t ws_bytes, uint32_t wait_limit_us, uint32_t missing_arrivals,
+                      kq_stream_t stream)
+{
+    Layout L;
+    if (!ws_ok(ws, ws_bytes, &L)) return KQ_EINVAL;
+    set_wait_fields<<<1, 1, 0, (cudaStream_t)stream>>>(kq::at<kq::Ctl>(ws, L.ctl), wait_limit_us, missing_arrivals);
+    return cudaGetLastError() == cudaSuccess ? KQ_OK : KQ_ECUDA;
 }
 
 int kq_status_read(const void *ws, int32_t *h_status, kq_stream_t stream)

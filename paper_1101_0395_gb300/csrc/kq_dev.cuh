@@ -6,6 +6,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include "../../include/kq.h"
@@ -35,7 +36,9 @@ struct Ctl {
     uint32_t abort;            // set when a wait timed out: every wait then gives up
     int64_t n_unique_true;     // N' before clamping to the caller's capacity
     unsigned long long ndc;    // distance calculations of the current kq_lloyd call
-    uint32_t pad0[26];
+    uint32_t wait_limit_us;    // device-side wait limit of the following launches (0: kWaitNs)
+    uint32_t missing;          // arrivals every wait expects beyond the launched blocks (test hook; 0)
+    uint32_t pad0[24];
     uint32_t bar_count;        // grid barrier: arrivals since the launch (cleared before each launch)
     uint32_t pad1[31];
     uint32_t bar_gen;          // unused
@@ -47,6 +50,7 @@ struct Ctl {
     uint32_t pad3[18];
 };
 static_assert(sizeof(Ctl) <= 4096, "control block must fit its region");
+static_assert(offsetof(Ctl, bar_count) == 128, "the barrier counter has its own 128-byte line");
 
 // ---------------------------------------------------------------- workspace layout
 struct Layout {
@@ -147,14 +151,22 @@ __device__ __forceinline__ void red_release_add_gpu(uint32_t *p, uint32_t v)
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Barrier over the first `nblocks` blocks of a cooperative launch.  The arrival
-// counter starts at 0 (the launcher clears it on the stream before the launch)
-// and only grows: barrier m of the launch is passed once it reaches
-// (m + 1) * nblocks, which the caller tracks in `*epoch`.  Thread 0 of each block
-// arrives with one release reduction and polls with acquire loads.  Every wait is
-// bounded: after kWaitNs, or when another block has given up, it records
-// KQ_ETIMEOUT, raises `abort` and returns false; the caller then returns.
-__device__ __forceinline__ bool grid_sync(Ctl *ctl, unsigned nblocks, uint32_t *epoch)
+// The wait limit of a launch (read once at its start).
+__device__ __forceinline__ uint64_t wait_limit_ns(const Ctl *ctl)
+{
+    const uint32_t us = *(volatile const uint32_t *)&ctl->wait_limit_us;
+    return us ? (uint64_t)us * 1000ull : kWaitNs;
+}
+
+// Barrier over `nblocks` blocks of a cooperative launch (normally all the blocks
+// taking part; more only when the test hook Ctl::missing asks for arrivals that
+// never come).  The arrival counter starts at 0 (the launcher clears it on the
+// stream before the launch) and only grows: barrier m of the launch is passed once
+// it reaches (m + 1) * nblocks, which the caller tracks in `*epoch`.  Thread 0 of
+// each block arrives with one release reduction and polls with acquire loads.
+// Every wait is bounded: after `limit_ns`, or when another block has given up, it
+// records KQ_ETIMEOUT, raises `abort` and returns false; the caller then returns.
+__device__ __forceinline__ bool grid_sync(Ctl *ctl, unsigned nblocks, uint32_t *epoch, uint64_t limit_ns)
 {
     __shared__ int s_ok;
     *epoch += nblocks;
@@ -169,7 +181,7 @@ __device__ __forceinline__ bool grid_sync(Ctl *ctl, unsigned nblocks, uint32_t *
                 if (ld_acquire_gpu(&ctl->abort)) { ok = 0; break; }
                 const uint64_t now = globaltimer_ns();
                 if (t0 == 0) t0 = now;
-                else if (now - t0 > kWaitNs) {
+                else if (now - t0 > limit_ns) {
                     fail(ctl, KQ_ETIMEOUT);
                     atomicExch(&ctl->abort, 1u);
                     ok = 0;

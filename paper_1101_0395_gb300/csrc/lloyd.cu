@@ -11,7 +11,10 @@
 //      row table rounded down make the stop conservative under FP32 rounding, so the
 //      labels equal a full FP32 search with the lowest index winning ties.  Each
 //      block accumulates exact integer sums (w R, w G, w B, w) per cluster in shared
-//      memory, its FP64 SSE partial and its distance count.
+//      memory, its distance count, and its FP32 SSE partial: a fixed-order tree (per
+//      32-colour chunk, then over the block's chunks in slot order, where the pruned
+//      pass balances its chunks over the warps), so the sum is deterministic; the
+//      blocks' partials are added in block order, also in FP32.
 //   -- grid barrier --
 //   B. update: every block evaluates SSE_i (a fixed-order sum of the block
 //      partials) and the stopping test of Section 3.3 identically; block b divides
@@ -22,8 +25,6 @@
 //      squared centre-to-centre distance table, each sorted ascending and packed as
 //      (distance bits with the low 8 cleared) | index.
 //   -- grid barrier (pruning only) --
-#include <mutex>
-
 #include "lloyd_body.cuh"
 
 namespace kq {
@@ -32,9 +33,10 @@ namespace {
 // One grid barrier over the first G blocks of the cooperative launch.
 struct GridSync {
     Ctl *ctl;
-    uint32_t G;
+    uint32_t G;  // blocks the barrier waits for
     uint32_t epoch;
-    __device__ __forceinline__ bool operator()() { return grid_sync(ctl, G, &epoch); }
+    uint64_t limit_ns;
+    __device__ __forceinline__ bool operator()() { return grid_sync(ctl, G, &epoch, limit_ns); }
 };
 
 __global__ void __launch_bounds__(kLloydBlock, 1) lloyd_kernel(LloydArgs a)
@@ -46,7 +48,7 @@ __global__ void __launch_bounds__(kLloydBlock, 1) lloyd_kernel(LloydArgs a)
     int64_t want = (n + (int64_t)kLloydBlock * kPtsPerThread - 1) / ((int64_t)kLloydBlock * kPtsPerThread);
     const int G = (int)(want < 1 ? 1 : (want > gridDim.x ? gridDim.x : want));
     if ((int)blockIdx.x >= G) return;
-    GridSync sync{a.ctl, (uint32_t)G, 0u};
+    GridSync sync{a.ctl, (uint32_t)G + *(volatile const uint32_t *)&a.ctl->missing, 0u, wait_limit_ns(a.ctl)};
     lloyd_body(a, sh, row_cache, n, (int)blockIdx.x, G, sync);
 }
 
@@ -120,24 +122,16 @@ static_assert(sizeof(Ctl) <= kNoAllocSums, "control block fits its slot");
 // Shared by every call on a device and kept for the life of the process.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-constexpr int kNoAllocDevices = 64;
-void *g_noalloc_ptr[kNoAllocDevices];
-std::mutex g_noalloc_mu;
-
-// Device address of the scratch array on the current device.  The host-side
+// Device address of the scratch array in the current context.  The host-side
 // name g_noalloc_scratch is only a stand-in for the symbol; the address comes
-// from cudaGetSymbolAddress, once per device, with that device current.
+// from cudaGetSymbolAddress with the caller's device current.  It is looked up on
+// every call (a host-side query that allocates nothing), so a context that was
+// destroyed and created again (cudaDeviceReset) never sees a stale address.
 int noalloc_scratch(void **out)
 {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocDevices) return KQ_ECUDA;
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return KQ_ECUDA;
-        g_noalloc_ptr[dev] = p;
-    }
-    *out = g_noalloc_ptr[dev];
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return KQ_ECUDA;
+    *out = p;
     return KQ_OK;
 }
 

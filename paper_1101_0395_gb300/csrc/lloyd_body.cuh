@@ -445,6 +445,22 @@ __device__ __forceinline__ void dense_step(const LloydArgs &a, LloydShared &sh, 
     }
 }
 
+// Statistics of a run that stopped because a barrier wait gave up (block 0).
+__device__ __forceinline__ void lloyd_failed_stats(const LloydArgs &a, int64_t n, int it)
+{
+    if (threadIdx.x != 0 || !a.stats) return;
+    const int32_t s = *(volatile const int32_t *)a.status;
+    kq_lloyd_stats st;
+    st.iters = it;
+    st.converged = 0;
+    st.k_eff = (int32_t)(n < a.K ? n : a.K);
+    st.status = s ? s : KQ_ETIMEOUT;
+    st.ndc = 0;
+    st.sse = 0.0;
+    st.sse_prev = 0.0;
+    *a.stats = st;
+}
+
 template <class Sync>
 __device__ __forceinline__ void lloyd_body(const LloydArgs &a, LloydShared &sh, uint32_t *row_cache, int64_t n, int b,
                                            int G, Sync &sync)
@@ -488,7 +504,10 @@ __device__ __forceinline__ void lloyd_body(const LloydArgs &a, LloydShared &sh, 
         for (int j = tid; j < 3 * kMaxK * 4; j += kLloydBlock) a.sums[j] = 0ull;
         if (tid == 0) *a.ndc = 0ull;
     }
-    if (!sync()) return;
+    if (!sync()) {
+        if (b == 0) lloyd_failed_stats(a, n, 0);
+        return;
+    }
 
     double prev_sse = 0.0;
     int it = 0;
@@ -691,7 +710,10 @@ __device__ __forceinline__ void lloyd_body(const LloydArgs &a, LloydShared &sh, 
             a.sse_part[(size_t)buf * kMaxGrid + b] = bsse;
             atomicAdd(a.ndc, bndc);
         }
-        if (!sync()) return;
+        if (!sync()) {
+            if (b == 0) lloyd_failed_stats(a, n, it);
+            return;
+        }
 
         // ---- B: SSE, stopping test, owned centres.  FP64 instructions are slow on
         // this GPU, so the stopping test (warp 0) and the three channel divisions of
@@ -763,14 +785,20 @@ __device__ __forceinline__ void lloyd_body(const LloydArgs &a, LloydShared &sh, 
         }
         if (stop) return;
         prev_sse = sse_i;
-        if (!sync()) return;
+        if (!sync()) {
+            if (b == 0) lloyd_failed_stats(a, n, it);
+            return;
+        }
 
         // ---- C: all centres, then this block's rows of the distance table
         for (int k = tid; k < K; k += kLloydBlock) set_centre(sh, k, __ldcg(a.cent + k));
         __syncthreads();
         if (prune) {
             build_rows(sh, K, b, G, a.rows);
-            if (!sync()) return;
+            if (!sync()) {
+                if (b == 0) lloyd_failed_stats(a, n, it);
+                return;
+            }
         }
     }
 }

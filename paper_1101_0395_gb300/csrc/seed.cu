@@ -219,6 +219,8 @@ __global__ void __launch_bounds__(kFarBlock, 1) seed_far(FarArgs a)
     if (b >= G) return;
     Ctl *ctl = a.ctl;
     uint32_t bar_epoch = 0;
+    const uint32_t bar_n = (uint32_t)G + *(volatile const uint32_t *)&ctl->missing;
+    const uint64_t limit_ns = wait_limit_ns(ctl);
     if (n > a.max_unique) {
         if (b == 0 && threadIdx.x == 0) fail(ctl, KQ_ENOMEM);
         return;
@@ -322,7 +324,7 @@ __global__ void __launch_bounds__(kFarBlock, 1) seed_far(FarArgs a)
                 if (lane == 0 && acc) atomicMax(a.slot + r, acc);
             }
         }
-        if (!grid_sync(ctl, G, &bar_epoch)) return;
+        if (!grid_sync(ctl, bar_n, &bar_epoch, limit_ns)) return;
         if (a.mode == 0) {
             if (warp == 0) {
                 const uint32_t k = far_locate(a, G, n, gstride, buf, rand64(a.seed, 2, (uint32_t)r), r == 0);
@@ -339,37 +341,64 @@ __global__ void __launch_bounds__(kFarBlock, 1) seed_far(FarArgs a)
 }
 
 // ---------------------------------------------------------------- KPP / MMX in one cluster
-// For N' up to kClusterCtas * kClPer colours, one thread-block cluster runs every
-// round.  Each CTA keeps its slice (keys, weights, D^2 in two buffers) in shared
-// memory; per round it writes the inclusive prefix sums of its threads' w D^2
-// (k-means++) or its packed maximum (minmax), passes one hardware cluster barrier,
-// and then reads what it needs from the other CTAs' shared memory (DSMEM): the
-// CTA totals, a 32-ary search over the chosen CTA's thread prefixes and that
-// thread's colours.  Every CTA computes the same next centre.  Buffers alternate
-// by round, so a CTA that starts the next round never overwrites what another CTA
-// may still be reading.
-constexpr int kClBlock = 1024;
-constexpr int kClElems = 11;                       // colours per thread at most (odd: see kernel)
-constexpr int kClPer = kClBlock * kClElems;        // colours per CTA (11264)
+// For N' up to C * kClPer colours (C = 16, else 8), one thread-block cluster runs
+// every round.  Each CTA holds a contiguous slice of the unique colours, thread t
+// a contiguous run of it: keys, weights, |x|^2 and D^2 stay in registers, and for
+// k-means++ the running sum of w D^2 over the thread's colours goes to shared
+// memory next to the keys.
+//
+// A round needs no whole-cluster barrier.  Its exchanges are pushes:
+//  1. every warp sends its total of w D^2 (k-means++) or its packed (D^2, key)
+//     maximum (minmax) to every CTA of the cluster with st.async, whose
+//     complete_tx counts the bytes on the receiving CTA's "data" mbarrier;
+//  2. minmax: once the data barrier has every warp's value, warp 0 takes the
+//     maximum, which holds the next centre's key;
+//     k-means++: warp 0 finds, from the CTA totals, the CTA g that holds the
+//     sample (t = below(u, sum) falls in its range).  Only CTA g goes on to find
+//     the warp, the thread and the colour -- all in its own shared memory -- and
+//     sends the key to every CTA with st.async on their "key" mbarrier;
+//  3. warp 0 passes the key to the other warps of its CTA (one __syncthreads).
+// Only warp 0 waits on the mbarriers (waiting warps would take issue slots from
+// the warps still working).  Each mbarrier exists twice and serves the rounds of
+// one parity; warp 0 re-arms the barrier of round r (expect_tx for round r + 2)
+// as soon as it has seen round r complete.  Pushes for round r + 2 cannot come
+// earlier: they need every warp of this CTA to have pushed round r + 1, which
+// each does after the __syncthreads that follows warp 0's waits of round r.  The
+// same argument makes one copy of the running sums enough: CTA g reads them
+// before it sends the key, and its warps rewrite them only after the key came.
+// Every wait is bounded (kWaitNs, or the control block's wait_limit_us); when
+// warp 0 gives up it records KQ_ETIMEOUT and the whole CTA leaves the rounds;
+// all CTAs then meet at the final cluster barrier, so no CTA exits while another
+// can still write to it.
+constexpr int kClBlock = 512;
+constexpr int kClWarps = kClBlock / 32;
+constexpr int kClElems = 22;                 // colours per thread at most
+constexpr int kClPer = kClBlock * kClElems;  // colours per CTA (11264)
+// shared-memory slots per array: thread t uses t * (EPT | 1) + k, k < EPT <= kClElems
+constexpr int kClSlots = kClBlock * (kClElems | 1);
+constexpr int kClMaxCtas = 16;
 
 struct ClusterArgs {
     const uint32_t *keys;
     const uint32_t *w;
     const int32_t *n_unique;
     int K;
-    int mode;       // 0 = k-means++, 1 = minmax
-    int ctas;       // cluster size
+    int mode;  // 0 = k-means++, 1 = minmax
+    int ctas;  // cluster size: 8 or 16
     uint64_t seed;
     double *centers;
     Ctl *ctl;
 };
 
 struct ClusterShared {
-    unsigned long long tpre[2][kClBlock];       // warp-local inclusive prefix of thread sums (k-means++)
-    // every CTA's warp totals / maxima, pushed by their owners; rows padded to 33 so
-    // that lane l reading slots 16 l .. 16 l + 15 does not hit one bank
-    unsigned long long wtot[2][16][kClBlock / 32 + 1];
-    uint32_t key;
+    unsigned long long tpre[kClBlock];  // k-means++: warp-local inclusive prefix of the threads' sums
+    // every CTA's warp totals (k-means++) or maxima (minmax), pushed by their warps;
+    // rows padded to 17 entries
+    unsigned long long wtot[2][kClMaxCtas][kClWarps + 1];
+    unsigned long long bar_data[2];  // mbarriers: all C x 16 warp values of a round have arrived
+    unsigned long long bar_key[2];   // mbarriers: the round's k-means++ sample has arrived
+    uint32_t key[2];                 // the round's centre: pushed by CTA g (k-means++) or set by warp 0 (minmax)
+    int dead;                        // warp 0 gave up waiting
 };
 
 __device__ __forceinline__ uint32_t cluster_rank()
@@ -384,185 +413,347 @@ __device__ __forceinline__ void cluster_sync_all()
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// The shared::cluster address of the same variable in CTA `rank`.
 __device__ __forceinline__ uint32_t dsmem_addr(const void *local, uint32_t rank)
 {
     uint32_t out;
-    const uint32_t a = (uint32_t)__cvta_generic_to_shared(local);
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(out) : "r"(a), "r"(rank));
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(out) : "r"(smem_u32(local)), "r"(rank));
     return out;
 }
 
-__device__ __forceinline__ unsigned long long dsmem_ld64(uint32_t addr)
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
 {
-    unsigned long long v;
-    asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(addr) : "memory");
-    return v;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
 }
 
-__device__ __forceinline__ uint32_t dsmem_ld32(uint32_t addr)
+// One arrival on the current phase, which also expects `bytes` of transactions.
+__device__ __forceinline__ void mbar_arrive_expect(uint32_t bar, uint32_t bytes)
 {
-    uint32_t v;
-    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
-    return v;
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.release.cta.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
+                     bar),
+                 "r"(bytes)
+                 : "memory");
 }
 
-__device__ __forceinline__ void dsmem_st64(uint32_t addr, unsigned long long v)
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity)
 {
-    asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(addr), "l"(v) : "memory");
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Waits (whole warp) until the phase of `bar` with the given parity has completed.
+// Gives up after limit_ns: records KQ_ETIMEOUT and returns false.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, Ctl *ctl, uint64_t limit_ns)
+{
+    uint64_t t0 = 0;
+    for (uint32_t spin = 0;; ++spin) {
+        if (__all_sync(kFull, mbar_test(bar, parity))) return true;
+        if ((spin & 15u) == 15u) {
+            int give_up = 0;
+            if ((threadIdx.x & 31) == 0) {
+                const uint64_t now = globaltimer_ns();
+                if (t0 == 0) t0 = now;
+                else if (now - t0 > limit_ns) give_up = 1;
+            }
+            if (__shfl_sync(kFull, give_up, 0)) {
+                if ((threadIdx.x & 31) == 0) fail(ctl, KQ_ETIMEOUT);
+                return false;
+            }
+        }
+    }
+}
+
+// st.async of one value into CTA-shared memory of a cluster peer; the receiving
+// mbarrier's transaction count goes down by the value's size once it has landed.
+__device__ __forceinline__ void push_u64(uint32_t addr, unsigned long long v, uint32_t bar)
+{
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b64 [%0], %1, [%2];" ::"r"(addr), "l"(v),
+                 "r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void push_u32(uint32_t addr, uint32_t v, uint32_t bar)
+{
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(addr), "r"(v),
+                 "r"(bar)
+                 : "memory");
+}
+
+// Inclusive scan over the first 2^S lanes (the other lanes add nothing useful).
+template <int S>
+__device__ __forceinline__ unsigned long long warp_incl_scan_u64(unsigned long long x, int lane)
+{
+#pragma unroll
+    for (int o = 1; o < (1 << S); o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long x)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(kFull, x, o);
+        x = y > x ? y : x;
+    }
+    return x;
+}
+
+// Sum (k-means++) or maximum (minmax) per CTA of the C x 16 pushed warp values:
+// lane l covers CTA l / (32 / C) and C / 2 of its warps; the result for CTA c is
+// returned in lane c (lanes >= C get copies).
+template <bool KPP>
+__device__ __forceinline__ unsigned long long cta_values(const ClusterShared &sh, int b, int C, int lane)
+{
+    const int lpc = 32 / C;  // lanes per CTA: 2 or 4
+    const int c = lane / lpc, part = lane % lpc, per = kClWarps / lpc;
+    const unsigned long long *row = &sh.wtot[b][c][part * per];
+    unsigned long long s = 0ull;
+#pragma unroll
+    for (int q = 0; q < kClWarps / 2; ++q) {
+        if (q < per) {
+            const unsigned long long v = row[q];
+            if (KPP) s += v;
+            else s = v > s ? v : s;
+        }
+    }
+#pragma unroll
+    for (int o = 1; o < 4; o <<= 1) {
+        if (o < lpc) {
+            const unsigned long long y = __shfl_down_sync(kFull, s, o);
+            if (KPP) s += y;
+            else s = y > s ? y : s;
+        }
+    }
+    return __shfl_sync(kFull, s, (lane % C) * lpc);
+}
+
+// The K rounds of one CTA whose threads hold EPT or EPT - 1 colours each.  The CTA's
+// `cnt` colours start at global index lo; thread t holds base + (t < rem) of them,
+// from position t * base + min(t, rem), and keeps their keys (and running sums) in
+// shared memory at t * kEps + k (an odd stride: a warp's accesses hit distinct banks).
+template <int EPT, bool KPP>
+__device__ __forceinline__ void cluster_rounds(const ClusterArgs &a, ClusterShared &sh, uint32_t *s_key,
+                                               uint32_t *s_aux, unsigned long long *s_pre, int64_t lo, int cnt, int C,
+                                               uint32_t rank, int64_t n)
+{
+    constexpr int kEps = EPT | 1;
+    // up to 16 colours per thread |x|^2 and the weights stay in registers; above that
+    // |x|^2 is recomputed and the weights are read from shared memory (no spills)
+    constexpr bool kNormRegs = EPT <= 16;
+    constexpr int kNr = kNormRegs ? EPT : 1;
+    const int K = a.K, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int base = cnt / kClBlock, rem = cnt % kClBlock;
+    const int mine = base + (tid < rem ? 1 : 0);  // EPT or EPT - 1
+    const int64_t start = lo + (int64_t)tid * base + (tid < rem ? tid : rem);
+    uint32_t key[EPT], aux[kNr], nrm[kNr], d2[EPT];  // aux: weight (k-means++) or 0xFFFFFF - key (minmax)
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+        key[k] = 0u;
+        if (kNormRegs) aux[k < kNr ? k : 0] = 0u;
+        d2[k] = 0xFFFFFFFFu;
+        if (k < mine) {
+            key[k] = a.keys[start + k];
+            const uint32_t ax = KPP ? a.w[start + k] : 0xFFFFFFu - key[k];
+            if (kNormRegs) aux[k < kNr ? k : 0] = ax;
+            else s_aux[tid * kEps + k] = ax;
+            s_key[tid * kEps + k] = key[k];
+        }
+        if (kNormRegs) nrm[k < kNr ? k : 0] = key_norm2(key[k]);
+    }
+    // a round's warp values, plus one per arrival the test hook Ctl::missing asks for
+    const uint32_t data_bytes =
+        ((uint32_t)C * kClWarps + *(volatile const uint32_t *)&a.ctl->missing) * (uint32_t)sizeof(unsigned long long);
+    const uint64_t limit_ns = wait_limit_ns(a.ctl);
+    // addresses of the round-parity b copies: the b = 0 address plus b times the stride
+    constexpr uint32_t kWtotStride = sizeof(sh.wtot[0]);
+    const uint32_t bar_data0 = smem_u32(&sh.bar_data[0]), bar_key0 = smem_u32(&sh.bar_key[0]);
+    if (tid == 0) {
+        for (uint32_t b = 0; b < 2; ++b) {
+            mbar_init(bar_data0 + 8u * b, 1);
+            mbar_init(bar_key0 + 8u * b, 1);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        for (uint32_t b = 0; b < 2; ++b) {
+            mbar_arrive_expect(bar_data0 + 8u * b, data_bytes);
+            mbar_arrive_expect(bar_key0 + 8u * b, (uint32_t)sizeof(uint32_t));
+        }
+        sh.dead = 0;
+    }
+    // Lane c < C sends to CTA c: this warp's slot and the barriers there.
+    uint32_t to_wtot = 0u, to_data = 0u, to_key = 0u, to_kbar = 0u;
+    if (lane < C) {
+        to_wtot = dsmem_addr(&sh.wtot[0][rank][warp], (uint32_t)lane);
+        to_data = dsmem_addr(&sh.bar_data[0], (uint32_t)lane);
+        to_key = dsmem_addr(&sh.key[0], (uint32_t)lane);
+        to_kbar = dsmem_addr(&sh.bar_key[0], (uint32_t)lane);
+    }
+    // every CTA's barriers exist and are armed before anyone pushes
+    cluster_sync_all();
+
+    uint32_t ckey = 0u, cnorm = 0u;
+    for (int r = 0; r < K; ++r) {
+        const int b = r & 1;
+        const uint32_t ph = (uint32_t)(r >> 1) & 1u;
+        // ---- this thread's colours: D^2 to the newest centre; w D^2 running sums or the packed maximum
+        unsigned long long acc = 0ull;
+        if (r > 0) {
+#pragma unroll
+            for (int k = 0; k < EPT; ++k) {
+                if (k < EPT - 1 || k < mine) {
+                    const uint32_t nk = kNormRegs ? nrm[k < kNr ? k : 0] : key_norm2(key[k]);
+                    const uint32_t d = nk + cnorm - 2u * __dp4a(key[k], ckey, 0u);
+                    const uint32_t md = min(d2[k], d);
+                    d2[k] = md;
+                    const uint32_t ax = kNormRegs ? aux[k < kNr ? k : 0] : s_aux[tid * kEps + k];
+                    if (KPP) {
+                        acc += (unsigned long long)ax * md;
+                        s_pre[tid * kEps + k] = acc;
+                    } else {
+                        const unsigned long long pk = ((unsigned long long)md << 24) | ax;
+                        acc = pk > acc ? pk : acc;
+                    }
+                }
+            }
+        } else if (KPP) {
+#pragma unroll
+            for (int k = 0; k < EPT; ++k) {
+                if (k < EPT - 1 || k < mine) {
+                    acc += kNormRegs ? aux[k < kNr ? k : 0] : s_aux[tid * kEps + k];  // first centre: w / sum w
+                    s_pre[tid * kEps + k] = acc;
+                }
+            }
+        }
+        // ---- the warp's total (with the threads' prefixes) or maximum, pushed to every CTA
+        unsigned long long wv;
+        if (KPP) {
+            const unsigned long long x = warp_incl_scan_u64<5>(acc, lane);
+            sh.tpre[tid] = x;
+            wv = __shfl_sync(kFull, x, 31);
+        } else {
+            wv = warp_max_u64(acc);
+        }
+        __syncwarp();  // the lanes' shared-memory writes above precede the pushes below
+        if (lane < C) push_u64(to_wtot + kWtotStride * (uint32_t)b, wv, to_data + 8u * (uint32_t)b);
+        if (warp == 0) {
+            const uint64_t u = KPP ? rand64(a.seed, 2, (uint32_t)r) : rand64(a.seed, 3, 0);
+            bool alive = mbar_wait(bar_data0 + 8u * (uint32_t)b, ph, a.ctl, limit_ns);
+            if (tid == 0 && alive) mbar_arrive_expect(bar_data0 + 8u * (uint32_t)b, data_bytes);  // re-arm for r + 2
+            if (!KPP) {
+                // minmax: the largest packed (D^2, key) of the cluster
+                uint32_t next;
+                if (r == 0) {
+                    next = __ldg(a.keys + below(u, (uint64_t)n));
+                } else {
+                    const unsigned long long m = warp_max_u64(cta_values<false>(sh, b, C, lane));
+                    next = 0xFFFFFFu - (uint32_t)(m & 0xFFFFFFull);
+                }
+                if (lane == 0) sh.key[b] = next;
+            } else if (alive) {
+                const unsigned long long ct = cta_values<true>(sh, b, C, lane);
+                const unsigned long long x = warp_incl_scan_u64<4>(lane < C ? ct : 0ull, lane);
+                const unsigned long long t = below(u, __shfl_sync(kFull, x, C - 1));
+                int g = __ffs(__ballot_sync(kFull, lane < C && x > t)) - 1;
+                g = g < 0 ? 0 : g;  // t < the total whenever it is positive
+                if (g == (int)rank) {
+                    // the warp of this CTA, then its thread, then the thread's colour
+                    const unsigned long long r1 = t - (__shfl_sync(kFull, x, g) - __shfl_sync(kFull, ct, g));
+                    const unsigned long long wtv = lane < kClWarps ? sh.wtot[b][g][lane] : 0ull;
+                    const unsigned long long xw = warp_incl_scan_u64<4>(wtv, lane);
+                    int ws = __ffs(__ballot_sync(kFull, lane < kClWarps && xw > r1)) - 1;
+                    ws = ws < 0 ? 0 : ws;
+                    const unsigned long long resid = r1 - (__shfl_sync(kFull, xw, ws) - __shfl_sync(kFull, wtv, ws));
+                    const unsigned long long s2 = sh.tpre[ws * 32 + lane];
+                    int l2 = __ffs(__ballot_sync(kFull, s2 > resid)) - 1;
+                    l2 = l2 < 0 ? 0 : l2;
+                    const unsigned long long prior = __shfl_sync(kFull, s2, l2 > 0 ? l2 - 1 : 0);
+                    const unsigned long long r2 = resid - (l2 > 0 ? prior : 0ull);
+                    const int ts = ws * 32 + l2;
+                    const int tcnt = base + (ts < rem ? 1 : 0);
+                    const unsigned long long pv = lane < tcnt ? s_pre[ts * kEps + lane] : ~0ull;
+                    int l3 = __ffs(__ballot_sync(kFull, pv > r2)) - 1;
+                    l3 = l3 < 0 ? 0 : l3;
+                    const uint32_t kk = lane == l3 ? s_key[ts * kEps + lane] : 0u;
+                    const uint32_t nk = __shfl_sync(kFull, kk, l3);
+                    if (lane < C) push_u32(to_key + 4u * (uint32_t)b, nk, to_kbar + 8u * (uint32_t)b);
+                }
+                alive = mbar_wait(bar_key0 + 8u * (uint32_t)b, ph, a.ctl, limit_ns);
+                if (tid == 0 && alive) mbar_arrive_expect(bar_key0 + 8u * (uint32_t)b, (uint32_t)sizeof(uint32_t));
+            }
+            if (!alive && lane == 0) sh.dead = 1;
+        }
+        __syncthreads();
+        if (sh.dead) break;  // the same for the whole CTA
+        ckey = sh.key[b];
+        cnorm = key_norm2(ckey);
+        if (rank == 0 && tid == 0) key_to_centre(a.centers + 3 * r, ckey);
+    }
+}
+
+template <bool KPP>
+__device__ __forceinline__ void cluster_dispatch(const ClusterArgs &a, ClusterShared &sh, uint32_t *s_key,
+                                                 uint32_t *s_aux, unsigned long long *s_pre, int64_t lo, int cnt, int C,
+                                                 uint32_t rank, int64_t n)
+{
+#define KQ_CL_CASE(E)                                                    \
+    case E: cluster_rounds<E, KPP>(a, sh, s_key, s_aux, s_pre, lo, cnt, C, rank, n); \
+        break;
+    switch ((cnt + kClBlock - 1) / kClBlock) {
+    case 0:
+        KQ_CL_CASE(1)
+        KQ_CL_CASE(2)
+        KQ_CL_CASE(3)
+        KQ_CL_CASE(4)
+        KQ_CL_CASE(5)
+        KQ_CL_CASE(6)
+        KQ_CL_CASE(7)
+        KQ_CL_CASE(8)
+        KQ_CL_CASE(9)
+        KQ_CL_CASE(10)
+        KQ_CL_CASE(11)
+        KQ_CL_CASE(12)
+        KQ_CL_CASE(13)
+        KQ_CL_CASE(14)
+        KQ_CL_CASE(15)
+        KQ_CL_CASE(16)
+        KQ_CL_CASE(17)
+        KQ_CL_CASE(18)
+        KQ_CL_CASE(19)
+        KQ_CL_CASE(20)
+        KQ_CL_CASE(21)
+    default: cluster_rounds<kClElems, KPP>(a, sh, s_key, s_aux, s_pre, lo, cnt, C, rank, n); break;
+    }
+#undef KQ_CL_CASE
 }
 
 __global__ void __launch_bounds__(kClBlock, 1) seed_far_cluster(ClusterArgs a)
 {
     __shared__ ClusterShared sh;
-    extern __shared__ uint32_t cl_smem[];  // key[kClPer], w[kClPer], d2[2][kClPer]
-    uint32_t *s_key = cl_smem, *s_w = cl_smem + kClPer, *s_d2 = cl_smem + 2 * kClPer;
+    extern __shared__ unsigned long long cl_smem[];  // running sums, keys, weights (or 0xFFFFFF - key): kClSlots each
+    unsigned long long *s_pre = cl_smem;
+    uint32_t *s_key = reinterpret_cast<uint32_t *>(cl_smem + kClSlots);
+    uint32_t *s_aux = s_key + kClSlots;
     const int64_t n = *a.n_unique;
     const int C = a.ctas;
     // this kernel serves K < N' <= C * kClPer; seed_far serves larger N'
     if (n <= a.K || n > (int64_t)C * kClPer) return;
-    const int K = a.K, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t rank = cluster_rank();
-    const int64_t per = (n + C - 1) / C;
-    const int64_t lo = (int64_t)rank * per < n ? (int64_t)rank * per : n;
-    const int cnt = (int)((lo + per < n ? lo + per : n) - lo);
-    // Thread t owns local colours [t ept, t ept + ept), stored at shared slots
-    // t eps + k with an odd stride eps >= ept, so a warp's accesses hit distinct banks.
-    const int ept = (cnt + kClBlock - 1) / kClBlock;
-    const int eps = ept | 1;
-    for (int j = tid; j < kClPer; j += kClBlock) {
-        s_key[j] = 0u;
-        s_w[j] = 0u;
-    }
-    __syncthreads();
-    for (int j = tid; j < cnt; j += kClBlock) {
-        const int slot = (j / ept) * eps + j % ept;
-        s_key[slot] = a.keys[lo + j];
-        s_w[slot] = a.w[lo + j];
-    }
-    __syncthreads();
-    uint32_t ckey = 0u, cnorm = 0u;
-    for (int r = 0; r < K; ++r) {
-        const int buf = r & 1;
-        uint32_t *d2 = s_d2 + buf * kClPer;
-        const uint32_t *d2p = s_d2 + (buf ^ 1) * kClPer;
-        unsigned long long acc = 0ull;
-        if (r > 0 || a.mode == 0) {
-#pragma unroll 4
-            for (int k = 0; k < ept; ++k) {
-                const int j = tid * eps + k;
-                if (tid * ept + k < cnt) {
-                    if (r == 0) {
-                        acc += s_w[j];  // k-means++ first centre: probability w / sum w
-                    } else {
-                        const uint32_t key = s_key[j];
-                        const uint32_t d = key_dist2n(key, key_norm2(key), ckey, cnorm);
-                        const uint32_t md = r == 1 ? d : min(d2p[j], d);
-                        d2[j] = md;
-                        if (a.mode == 0) {
-                            acc += (unsigned long long)s_w[j] * md;
-                        } else {
-                            const unsigned long long pk = mmx_pack(md, key);
-                            acc = pk > acc ? pk : acc;
-                        }
-                    }
-                }
-            }
-        }
-        // warp scan (k-means++) or warp maximum (minmax); the warp's total is pushed
-        // into slot [rank][warp] of every CTA of the cluster
-        unsigned long long wv;
-        if (a.mode == 0) {
-            unsigned long long x = acc;
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned long long y = __shfl_up_sync(kFull, x, o);
-                if (lane >= o) x += y;
-            }
-            sh.tpre[buf][tid] = x;
-            wv = __shfl_sync(kFull, x, 31);
-        } else {
-            for (int o = 16; o; o >>= 1) {
-                const unsigned long long other = __shfl_xor_sync(kFull, acc, o);
-                acc = other > acc ? other : acc;
-            }
-            wv = acc;
-        }
-        if (lane < C) dsmem_st64(dsmem_addr(&sh.wtot[buf][rank][warp], lane), wv);
-        const uint64_t u = a.mode == 0 ? rand64(a.seed, 2, (uint32_t)r) : rand64(a.seed, 3, 0);
-        cluster_sync_all();
-        // Warp 0 of every CTA finds the next centre (reads only this round's buffers,
-        // which nobody writes before the next cluster barrier) and shares it.
-        uint32_t next = 0u;
-        if (warp != 0) {
-        } else if (a.mode == 1) {
-            if (r == 0) {
-                next = a.keys[below(u, (uint64_t)n)];
-            } else {
-                unsigned long long m = 0ull;
-                if (lane < C)
-                    for (int q = 0; q < kClBlock / 32; ++q) m = sh.wtot[buf][lane][q] > m ? sh.wtot[buf][lane][q] : m;
-                for (int o = 16; o; o >>= 1) {
-                    const unsigned long long other = __shfl_xor_sync(kFull, m, o);
-                    m = other > m ? other : m;
-                }
-                next = 0xFFFFFFu - (uint32_t)(m & 0xFFFFFFull);
-            }
-        } else {
-            // CTA totals (lane c sums CTA c's 32 warp totals), then the sampled CTA
-            unsigned long long ct = 0ull;
-            if (lane < C)
-                for (int q = 0; q < kClBlock / 32; ++q) ct += sh.wtot[buf][lane][q];
-            unsigned long long x = ct;
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned long long y = __shfl_up_sync(kFull, x, o);
-                if (lane >= o) x += y;
-            }
-            const unsigned long long t = below(u, __shfl_sync(kFull, x, 31));
-            const int g = __ffs(__ballot_sync(kFull, lane < C && x > t)) - 1;
-            const unsigned long long r1 = t - (__shfl_sync(kFull, x, g) - __shfl_sync(kFull, ct, g));
-            // the warp of CTA g
-            const unsigned long long wt = sh.wtot[buf][g][lane];
-            unsigned long long xw = wt;
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned long long y = __shfl_up_sync(kFull, xw, o);
-                if (lane >= o) xw += y;
-            }
-            const int ws = __ffs(__ballot_sync(kFull, xw > r1)) - 1;
-            const unsigned long long resid = r1 - (__shfl_sync(kFull, xw, ws) - __shfl_sync(kFull, wt, ws));
-            // the thread: warp-local inclusive prefixes, read from CTA g
-            const unsigned long long s2 = dsmem_ld64(dsmem_addr(&sh.tpre[buf][ws * 32 + lane], g));
-            const int l2 = __ffs(__ballot_sync(kFull, s2 > resid)) - 1;
-            const unsigned long long prior = l2 > 0 ? __shfl_sync(kFull, s2, l2 - 1) : 0ull;
-            const int ts = ws * 32 + l2;
-            const unsigned long long r2 = resid - prior;
-            // that thread's colours (CTA g's slice and colours per thread)
-            const int64_t glo = (int64_t)g * per;
-            const int gcnt = (int)((glo + per < n ? glo + per : n) - glo);
-            const int gept = (gcnt + kClBlock - 1) / kClBlock;
-            unsigned long long pk = 0ull;
-            uint32_t kk = 0u;
-            if (lane < gept) {
-                const int j = ts * (gept | 1) + lane;
-                if (ts * gept + lane < gcnt) {
-                    kk = dsmem_ld32(dsmem_addr(&s_key[j], g));
-                    const unsigned long long wj = dsmem_ld32(dsmem_addr(&s_w[j], g));
-                    pk = r == 0 ? wj : wj * (unsigned long long)dsmem_ld32(dsmem_addr(&d2[j], g));
-                }
-            }
-            unsigned long long xe = pk;
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned long long y = __shfl_up_sync(kFull, xe, o);
-                if (lane >= o) xe += y;
-            }
-            const int l3 = __ffs(__ballot_sync(kFull, lane < gept && xe > r2)) - 1;
-            next = __shfl_sync(kFull, kk, l3 < 0 ? 0 : l3);
-        }
-        if (tid == 0) sh.key = next;
-        __syncthreads();
-        ckey = sh.key;
-        cnorm = key_norm2(ckey);
-        if (rank == 0 && tid == 0) key_to_centre(a.centers + 3 * r, ckey);
-    }
-    // no CTA may leave while another can still read its shared memory
+    const int64_t cbase = n / C, crem = n % C;
+    const int64_t lo = (int64_t)rank * cbase + ((int64_t)rank < crem ? (int64_t)rank : crem);
+    const int cnt = (int)(cbase + ((int64_t)rank < crem ? 1 : 0));
+    if (a.mode == 0) cluster_dispatch<true>(a, sh, s_key, s_aux, s_pre, lo, cnt, C, rank, n);
+    else cluster_dispatch<false>(a, sh, s_key, s_aux, s_pre, lo, cnt, C, rank, n);
+    // no CTA leaves while another may still push into its shared memory
     cluster_sync_all();
 }
 
@@ -741,7 +932,7 @@ __global__ void __launch_bounds__(1024) seed_wu_split(const int32_t *n_unique, i
     wu_split_block(cum, K, centers, sh);
 }
 
-constexpr size_t kClSmem = sizeof(uint32_t) * 4 * (size_t)kClPer;  // keys, weights, 2 x D^2
+constexpr size_t kClSmem = (sizeof(unsigned long long) + 2 * sizeof(uint32_t)) * (size_t)kClSlots;  // sums, keys, aux
 
 // Largest cluster (16, else 8) of seed_far_cluster this device can run, or 0.
 int far_cluster_size()

@@ -72,6 +72,7 @@ _SIGS = {
                                        _vp, C.c_size_t, _vp]),
     "kq_status_read": (C.c_int, [_vp, C.POINTER(C.c_int32), _vp]),
     "kq_status_clear": (C.c_int, [_vp, _vp]),
+    "kq_set_wait_limit": (C.c_int, [_vp, C.c_size_t, C.c_uint32, C.c_uint32, _vp]),
     "kq_strerror": (C.c_char_p, [C.c_int]),
     "kq_batch_scratch_bytes": (C.c_size_t, [C.c_int32]),
     "kq_batch_workspace_size": (C.c_size_t, []),
@@ -187,6 +188,11 @@ def kq_status_read(ws: torch.Tensor, stream=None) -> int:
     v = C.c_int32(0)
     _check("kq_status_read", lib().kq_status_read(_ptr(ws), C.byref(v), _stream(stream)))
     return int(v.value)
+
+
+def kq_set_wait_limit(ws: torch.Tensor, wait_limit_us: int, missing_arrivals: int = 0, stream=None) -> None:
+    _check("kq_set_wait_limit", lib().kq_set_wait_limit(_ptr(ws), ws.numel() * ws.element_size(), int(wait_limit_us),
+                                                        int(missing_arrivals), _stream(stream)))
 
 
 def kq_status_clear(ws: torch.Tensor, stream=None) -> None:

@@ -3,6 +3,7 @@ seeded inputs and bring results back as numpy arrays."""
 import numpy as np
 import torch
 
+import oracle
 from paper_1101_0395_gb300 import kq
 
 # Match rules (stated in the task contract and derived in the design notes):
@@ -101,3 +102,36 @@ def check_labels(keys, centers, gpu_labels, ora_labels, d1, d2):
     dg = ((x - centers[gpu_labels[diff]]) ** 2).sum(axis=1)
     assert np.all(dg - d1[diff] <= tol), "GPU label is not one of the near-tied centres"
     return int(diff.size)
+
+
+def lockstep(r, keys, w, c0, passes, dense=False):
+    """Lloyd in lockstep with the oracle: every pass starts from the oracle's
+    centres (and, for the pruned search, its previous labels).  Labels agree
+    except at oracle near-ties; centres are the oracle's update of the GPU labels
+    (bit for bit); SSE within MSE_REL.  Returns the number of tolerated near-tie
+    flips and the last SSEs."""
+    c = np.array(c0, dtype=np.float64)
+    prev = None
+    flips = 0
+    sse_g = sse_o = None
+    for i in range(passes):
+        lab_o, d1, d2, sse_o = oracle.assign(keys, w, c)
+        c_next, sums = oracle.update(keys, w, lab_o, c)
+        if dense:
+            g = r.lloyd(c, eps=-1.0, max_iter=1, flags=kq.LLOYD_DENSE)
+        else:
+            g = r.lloyd(c, eps=-1.0, max_iter=1, flags=0 if prev is None else kq.LLOYD_LABELS_IN, labels_in=prev)
+        f = check_labels(keys, c, g["labels"], lab_o, d1, d2)
+        flips += f
+        sse_g = g["stats"]["sse"]
+        assert abs(sse_g - sse_o) <= MSE_REL * max(sse_o, 1.0), (i, sse_g, sse_o)
+        if f == 0:
+            assert np.array_equal(g["centers"], c_next), i
+            assert np.array_equal(g["palette"], oracle.palette(sums, c_next)), i
+        else:
+            c_on_gpu, _ = oracle.update(keys, w, g["labels"], c)
+            assert np.array_equal(g["centers"], c_on_gpu), i
+        assert np.max(np.abs(g["centers"] - c_next)) <= CENTER_ABS or f > 0
+        assert g["stats"]["iters"] == 1
+        prev, c = lab_o, c_next
+    return flips, sse_g, sse_o

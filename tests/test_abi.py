@@ -17,7 +17,7 @@ def test_exports_every_declared_symbol():
                           "kq_lloyd_noalloc", "kq_status_read", "kq_status_clear", "kq_strerror",
                           "kq_batch_scratch_bytes", "kq_batch_workspace_size", "kq_batch_max_cluster",
                           "kq_batch_plan", "kq_batch_run", "kq_batch_tune", "kq_pixel_keys",
-                          "kq_histogram_strided"}
+                          "kq_histogram_strided", "kq_set_wait_limit"}
     L = kq.lib()
     for n in names:
         assert getattr(L, n) is not None
@@ -59,6 +59,8 @@ def test_invalid_arguments_are_rejected_synchronously():
     assert L.kq_lloyd(None, p, p, 8, p, 1e-4, 10, 0, p, p, None, None, WS, size, None) == kq.KQ_EINVAL
     assert L.kq_map(p, 10, p, p, p, p, 8, None, None, WS, size, None) == kq.KQ_EINVAL
     assert L.kq_status_read(None, None, None) == kq.KQ_EINVAL
+    assert L.kq_set_wait_limit(None, size, 1000, 1, None) == kq.KQ_EINVAL
+    assert L.kq_set_wait_limit(WS, 4096, 1000, 1, None) == kq.KQ_EINVAL
     assert L.kq_workspace_init(None, size, None) == kq.KQ_EINVAL
 
 

@@ -85,7 +85,7 @@ def _check_item(bq, i, im, seed, res):
             c0, _ = oracle.seed(keys, w, K, scheme, seed)
         r = Run(im)
         r.histogram()
-        c, labels, hist, _ = gpu_trajectory(r, keys, w, c0, EPS, MAX_ITER)
+        c, labels, hist, _, _ = gpu_trajectory(r, keys, w, c0, EPS, MAX_ITER)
         assert st["iters"] == hist.size, (i, st["iters"], hist.size)
         assert np.array_equal(cen, c)
         assert np.array_equal(bq.labels(i)[:nu].cpu().numpy(), labels)

@@ -35,7 +35,7 @@ def test_quantizer_end_to_end(name, K):
     c0, _ = oracle.seed(keys, w, K, "KPP", BENCH_SEED)
     r = Run(img)
     r.histogram()
-    c, labels, hist, _ = gpu_trajectory(r, keys, w, c0, wl.eps, wl.max_iter)
+    c, labels, hist, _, _ = gpu_trajectory(r, keys, w, c0, wl.eps, wl.max_iter)
     st = kq.parse_stats(res.stats)
     assert st["iters"] == hist.size and st["sse"] == hist[-1]
     assert np.array_equal(res.centers.cpu().numpy(), c)
