@@ -54,6 +54,8 @@ def parse_args(argv=None):
     p.add_argument("--count", type=int, default=512, help="batched: images per batch")
     p.add_argument("--rate", type=float, default=200.0, help="serving: Poisson arrival rate (req/s)")
     p.add_argument("--duration", type=float, default=10.0, help="serving: arrival trace length (s)")
+    p.add_argument("--no-extras", action="store_true",
+                   help="default workload: skip the 4096x4096, batched and serving measurements")
     return p.parse_args(argv)
 
 
@@ -529,13 +531,13 @@ def run_table1(args, rank, world, local) -> None:
             kq.kq_histogram(rgb, q.keys, q.weights, q.n_unique, q.ws)
             c_w.copy_(c0)
             kq.kq_lloyd(q.keys, q.weights, q.n_unique, K, c_w, -1.0, 20, q.labels, pal_w, q.ws, stats=q.stats)
-            kq.kq_map(rgb, q.keys, q.weights, q.n_unique, pal_w, K, idx, q.ws, sse_num=q.sse_num)
+            kq.kq_map(rgb, pal_w, K, idx, q.ws, sse_num=q.sse_num)
 
         def km():
             kq.kq_pixel_keys(rgb, pk, pw, pn)
             c_k.copy_(c0)
             kq.kq_lloyd(pk, pw, pn, K, c_k, -1.0, 20, lab2, pal_k, ws2, stats=q.stats, flags=kq.LLOYD_DENSE)
-            kq.kq_map(rgb, q.keys, q.weights, q.n_unique, pal_k, K, idx, q.ws, sse_num=q.sse_num)
+            kq.kq_map(rgb, pal_k, K, idx, q.ws, sse_num=q.sse_num)
 
         t_w = timed(wsm)
         st_w = kq.parse_stats(q.stats)
@@ -564,7 +566,7 @@ def run_table1(args, rank, world, local) -> None:
                             stats=q.stats)
                 if stride != 1:
                     kq.kq_histogram(rgb, q.keys, q.weights, q.n_unique, q.ws)
-                kq.kq_map(rgb, q.keys, q.weights, q.n_unique, pal, K, idx, q.ws, sse_num=q.sse_num)
+                kq.kq_map(rgb, pal, K, idx, q.ws, sse_num=q.sse_num)
 
             t = timed(run)
             out[stride] = {"ms": t, "mse": int(q.sse_num.item()) / n, "iters": kq.parse_stats(q.stats)["iters"]}
@@ -581,6 +583,249 @@ def run_table1(args, rank, world, local) -> None:
             "rows": rows, "wsm_ms_by_K": sweep, "subsampling_2to1": sub, "gpu_launches": None}
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- extra measurements of the default run
+# The headline is the 512 x 512 image; the same JSON line also carries the kernels on
+# the 4096 x 4096 image (where the histogram and mapping bandwidth targets apply), a
+# size-stratified subset of the batched workload against the plain per-image path at
+# the same MSE, and a short serving trace against the plain server.
+EXTRA_BATCH = 64            # every 8th image, by size, of the 512-image batch spec
+EXTRA_SERVE_POOL = 12       # serving: images the requests pick from
+EXTRA_SERVE_RATE = 200.0    # req/s
+EXTRA_SERVE_SECONDS = 3.0
+
+
+def _gen_workload_image(args):
+    from paper_1101_0395_gb300 import synth
+
+    name, index = args
+    return synth.WORKLOADS[name].make(index)
+
+
+def extra_inputs():
+    """The extras' synthetic inputs, generated on all host cores (spawned workers, so
+    that no CUDA state is forked); called after the timed region."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+
+    from paper_1101_0395_gb300 import synth
+
+    spec = synth.batch_spec(512)
+    order = sorted(range(len(spec.sizes)), key=lambda i: spec.sizes[i][0] * spec.sizes[i][1])
+    pick = order[::len(order) // EXTRA_BATCH][:EXTRA_BATCH]
+    sub = synth.BatchSpec([spec.sizes[i] for i in pick], [spec.ks[i] for i in pick], [spec.seeds[i] for i in pick])
+    pool = synth.batch_spec(EXTRA_SERVE_POOL, side_lo=256, side_hi=4096, seed=4101, k_uniform_range=(8, 256))
+    with ProcessPoolExecutor(max_workers=os.cpu_count(), mp_context=mp.get_context("spawn")) as ex:
+        big = ex.submit(_gen_workload_image, ("large_4096", 0))
+        bf = [ex.submit(_gen_batch_image, (h, w, sd)) for (h, w), sd in zip(sub.sizes, sub.seeds)]
+        sf = [ex.submit(_gen_batch_image, (h, w, sd)) for (h, w), sd in zip(pool.sizes, pool.seeds)]
+        return big.result(), (sub, [f.result() for f in bf]), (pool, [f.result() for f in sf])
+
+
+def _median_ms(fn, flush, stream, reps=10, warm=3):
+    import torch
+
+    ts = []
+    for r in range(reps + warm):
+        flush.fill_(r & 255)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        if r >= warm:
+            ts.append(a.elapsed_time(b))
+    return float(statistics.median(ts))
+
+
+def extra_large(img, K, dev, fp32_peak, hbm_peak, alu_peak) -> dict:
+    """The 4096 x 4096 image: histogram and mapping against HBM, the full search
+    against the FP32 peak, seeding and pruned Lloyd times, the whole pipeline."""
+    import torch
+
+    from paper_1101_0395_gb300 import kq, synth
+
+    wl = synth.WORKLOADS["large_4096"]
+    n = img.size // 3
+    q = kq.Quantizer(n, device=dev)
+    rgb = torch.from_numpy(img.reshape(-1)).to(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    c = q.centers[:3 * K]
+    pal = q.palette[:3 * K]
+    t_hist = _median_ms(lambda: kq.kq_histogram(rgb, q.keys, q.weights, q.n_unique, q.ws), flush, stream)
+    nu = int(q.n_unique.item())
+    t_seed = _median_ms(lambda: kq.kq_seed(q.keys, q.weights, q.n_unique, K, SCHEME, SEED, c, q.ws), flush, stream,
+                        reps=5)
+    c0 = c.clone()
+
+    def lloyd(P, flags, eps):
+        def f():
+            c.copy_(c0)
+            kq.kq_lloyd(q.keys, q.weights, q.n_unique, K, c, eps, P, q.labels, pal, q.ws, stats=q.stats, flags=flags)
+        return f
+
+    d1 = _median_ms(lloyd(1, kq.LLOYD_DENSE, -1.0), flush, stream, reps=5)
+    d5 = _median_ms(lloyd(5, kq.LLOYD_DENSE, -1.0), flush, stream, reps=5)
+    t_lloyd = _median_ms(lloyd(wl.max_iter, 0, wl.eps), flush, stream, reps=5)
+    st = kq.parse_stats(q.stats)
+    t_map = _median_ms(lambda: kq.kq_map(rgb, pal, K, q.idx[:n], q.ws,
+                                         sse_num=q.sse_num), flush, stream)
+    map_ndc = kq.kq_map_ndc_read(q.ws)
+    t_all = _median_ms(lambda: q.quantize(rgb, K, SCHEME, SEED, wl.eps, wl.max_iter), flush, stream, reps=5)
+    if kq.kq_status_read(q.ws) != kq.KQ_OK:
+        raise RuntimeError("device status after the 4096x4096 runs: %s" % kq.strerror(kq.kq_status_read(q.ws)))
+    hist_b, map_b = 3.0 * n + 8.0 * nu, 4.0 * n + 8.0 * nu
+    pass_flop = float(FLOP_PER_DIST) * nu * K
+    kpp_ops = 5.0 * nu * K
+    return {
+        "workload": "large_4096: one 4096x4096 synthetic RGB8 image (512 regions plus global ramps), K=%d, %s seeds, "
+                    "eps=%g, <=%d passes; L2 flushed before every timed call" % (K, SCHEME, wl.eps, wl.max_iter),
+        "n_pixels": n, "n_unique": nu,
+        "pipeline": {"ms": t_all, "mpix_per_s": n / (t_all * 1e-3) / 1e6},
+        "histogram": {"ms": t_hist, "achieved": hist_b / (t_hist * 1e-3) / 1e9, "unit": "GB/s", "peak": hbm_peak,
+                      "frac": hist_b / (t_hist * 1e-3) / 1e9 / hbm_peak,
+                      "algorithmic": "3 B per pixel + 8 B per unique colour"},
+        "map": {"ms": t_map, "achieved": map_b / (t_map * 1e-3) / 1e9, "unit": "GB/s", "peak": hbm_peak,
+                "frac": map_b / (t_map * 1e-3) / 1e9 / hbm_peak, "ndc": map_ndc,
+                "ndc_per_colour": map_ndc / max(1, nu),
+                "algorithmic": "3 B in + 1 B out per pixel + 8 B per unique colour"},
+        "assignment_dense": {"one_pass_ms": d1, "five_pass_ms": d5,
+                             "achieved_5_passes": 5 * pass_flop / (d5 * 1e-3) / 1e12, "unit": "TFLOP/s",
+                             "peak": fp32_peak, "frac_5_passes": 5 * pass_flop / (d5 * 1e-3) / 1e12 / fp32_peak,
+                             "frac_marginal_pass": pass_flop / ((d5 - d1) / 4 * 1e-3) / 1e12 / fp32_peak
+                             if d5 > d1 else None,
+                             "algorithmic": "%d FLOP per distance x N' x K per pass" % FLOP_PER_DIST},
+        "seed_kpp": {"ms": t_seed, "us_per_round": 1e3 * t_seed / K,
+                     "achieved": kpp_ops / (t_seed * 1e-3) / 1e12, "unit": "Tops/s", "peak": alu_peak,
+                     "frac": kpp_ops / (t_seed * 1e-3) / 1e12 / alu_peak,
+                     "algorithmic": "5 integer operations per unique colour per round (distance by dp4a, "
+                                    "norm terms, minimum, weighted sum)"},
+        "lloyd_pruned": {"ms": t_lloyd, "passes": st["iters"], "ndc_per_colour_per_pass": st["ndc"] / max(1, nu * st["iters"]),
+                         "dense_equivalent_gdist_per_s": nu * K * st["iters"] / (t_lloyd * 1e-3) / 1e9},
+    }
+
+
+def extra_batched(sub, imgs, dev) -> dict:
+    """The batched form (one persistent launch, autotuned, CUDA graph) against the
+    plain per-image path on the same GPU and images, at the same MSE."""
+    import numpy as np
+    import torch
+
+    from paper_1101_0395_gb300 import kq
+
+    n_px = [im.size // 3 for im in imgs]
+    bq = kq.BatchQuantizer(n_px, sub.ks, SCHEME, sub.seeds, 1e-4, 100, device=dev)
+    for i, im in enumerate(imgs):
+        bq.rgb(i).copy_(torch.from_numpy(im.reshape(-1)))
+    torch.cuda.synchronize()
+    bq.tune()
+    bq.capture()
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        bq.replay()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(5):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        bq.replay()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    ms = float(statistics.median(ts))
+    res = bq.results()
+    if np.any(res["status"] != kq.KQ_OK):
+        raise RuntimeError("batch item errors: %s" % np.unique(res["status"]))
+    q = kq.Quantizer(max(n_px), device=dev)
+    sse_loop = []
+    lt = []
+    for rep in range(3):
+        sse_loop.clear()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for i in range(len(imgs)):
+            r = q.quantize(bq.rgb(i), sub.ks[i], SCHEME, sub.seeds[i], 1e-4, 100)
+            sse_loop.append(r.sse_num.clone())
+        b.record(stream)
+        torch.cuda.synchronize()
+        if rep:
+            lt.append(a.elapsed_time(b))
+    loop_ms = float(min(lt))
+    sse_b = res["sse_num"].astype(np.int64)
+    sse_l = np.array([int(x.item()) for x in sse_loop], dtype=np.int64)
+    shape = {"cluster": bq.cfg.cluster, "split_pixels": bq.cfg.split_pixels, "images_on_clusters": bq.n_big}
+    del bq
+    torch.cuda.empty_cache()
+    return {"workload": "%d of the 512 batch images (every 8th by size: %d..%d px), K from {16..256}, %s seeds, "
+                        "eps=1e-4, <=100 passes" % (len(imgs), min(n_px), max(n_px), SCHEME),
+            "images": len(imgs), "n_pixels": int(sum(n_px)), "launch_shape": shape,
+            "batched": {"ms": ms, "img_per_s": len(imgs) / (ms * 1e-3), "mpix_per_s": sum(n_px) / (ms * 1e-3) / 1e6,
+                        "mse": float(sse_b.sum() / sum(n_px))},
+            "per_image_path": {"ms": loop_ms, "img_per_s": len(imgs) / (loop_ms * 1e-3),
+                               "mpix_per_s": sum(n_px) / (loop_ms * 1e-3) / 1e6,
+                               "mse": float(sse_l.sum() / sum(n_px))},
+            "speedup": loop_ms / ms, "same_sse_images": int((sse_b == sse_l).sum())}
+
+
+def extra_serving(pool, imgs, dev) -> dict:
+    """A short Poisson trace through the server (continuous batching, memory
+    admission) and through the plain per-image server, same requests."""
+    import torch
+
+    from paper_1101_0395_gb300 import kq, serve, synth
+
+    arrivals = serve.poisson_arrivals(EXTRA_SERVE_RATE, EXTRA_SERVE_SECONDS, 4101)
+    u = synth.uniform(4101, 40, 2 * max(1, arrivals.size))
+    picks = (u[0::2] * len(imgs)).astype(int)
+    ks = 8 + (u[1::2] * 249).astype(int).clip(0, 248)
+    h_imgs = [torch.from_numpy(im.reshape(-1)).pin_memory() for im in imgs]
+    max_px = max(im.size // 3 for im in imgs)
+
+    def requests(count=None):
+        out = []
+        for i in range(arrivals.size if count is None else count):
+            out.append(serve.Request(rid=i, rgb=h_imgs[int(picks[i])], K=int(ks[i]), scheme=SCHEME, seed=1000 + i,
+                                     arrival=float(arrivals[i]) if count is None else 0.0))
+        return out
+
+    n_px = [im.size // 3 for im in imgs]
+    bq = kq.BatchQuantizer(n_px, [int(k) for k in ks[:len(imgs)]], SCHEME, list(range(len(imgs))), device=dev)
+    for i in range(len(imgs)):
+        bq.rgb(i).copy_(h_imgs[i])
+    bq.tune()
+    cluster, split = bq.cfg.cluster, bq.cfg.split_pixels
+    del bq
+    torch.cuda.empty_cache()
+    srv = serve.Server(serve.CudaBackend(cluster, split, device=dev, solo_max_pixels=max_px), 16 << 30, streams=2,
+                       max_wave=64, solo_queue=SOLO_QUEUE)
+    for r in requests(8):
+        srv.submit(r)
+    srv.drain()
+    srv.finished.clear()
+    reqs = requests()
+    out = serve.run_trace(srv, reqs)
+    waves, solo = srv.waves, srv.backend.solo_waves
+    del srv
+    torch.cuda.empty_cache()
+    plain = serve.Server(serve.PlainBackend(max_px, device=dev), 1 << 30, streams=1, max_wave=1)
+    for r in requests(4):
+        plain.submit(r)
+    plain.drain()
+    plain.finished.clear()
+    preqs = requests()
+    pout = serve.run_trace(plain, preqs)
+    same = sum(int(a.result["sse_num"]) == int(b.result["sse_num"]) for a, b in zip(reqs, preqs))
+    return {"workload": "Poisson arrivals at %g req/s for %g s; image side log-uniform 256-4096 (pool of %d), K uniform "
+                        "8..256, %s seeds, eps=1e-4, <=100 passes" % (EXTRA_SERVE_RATE, EXTRA_SERVE_SECONDS, len(imgs),
+                                                                     SCHEME),
+            "requests": len(reqs),
+            "server": {"p50_ms": out["p50_ms"], "p99_ms": out["p99_ms"], "img_per_s": out["img_per_s"],
+                       "mpix_per_s": out["mpix_per_s"], "waves": waves, "solo_waves": solo},
+            "plain_server": {"p50_ms": pout["p50_ms"], "p99_ms": pout["p99_ms"], "img_per_s": pout["img_per_s"],
+                             "mpix_per_s": pout["mpix_per_s"]},
+            "same_sse_requests": same}
 
 
 def run_reference(args, rank, world) -> None:
@@ -671,7 +916,7 @@ def run_gpu(args, rank, world, local) -> None:
         kq.kq_lloyd(quant.keys, quant.weights, quant.n_unique, K, c, wl.eps, wl.max_iter, quant.labels, pal,
                     quant.ws, stats=quant.stats)
         yield
-        kq.kq_map(src, quant.keys, quant.weights, quant.n_unique, pal, K, quant.idx[:n], quant.ws,
+        kq.kq_map(src, pal, K, quant.idx[:n], quant.ws,
                   sse_num=quant.sse_num)
         yield
 
@@ -743,7 +988,9 @@ def run_gpu(args, rank, world, local) -> None:
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz") or 2070.0)
     fp32_peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
+    alu_peak = fp32_peak / 2.0  # one 32-bit integer operation per lane per clock
     hbm_peak = float(peaks.get("hbm_gbs") or 6800.0)
+    hbm_source = "MEASURED_PEAKS hbm_gbs" if peaks.get("hbm_gbs") else "fallback 6800 GB/s (MEASURED_PEAKS.json absent)"
     names = ["kq_histogram", "kq_seed", "kq_lloyd", "kq_map"]
     dom = max(range(4), key=lambda j: stage_mean[j])
     lloyd_s = stage_mean[2] * 1e-3
@@ -758,28 +1005,32 @@ def run_gpu(args, rank, world, local) -> None:
                                % (props.multi_processor_count, sm_max),
                 "algorithmic": "%d FLOP per distance x NDC %d" % (FLOP_PER_DIST, st["ndc"])}
     elif dom == 1:
-        # k-means++ in one thread-block cluster: K sequential rounds, each refreshing the
-        # exact integer D^2 of every unique colour (one dp4a distance plus ~7 integer
-        # operations: 8 ALU operations per colour and round) between two cluster barriers.
-        # The slice lives in shared memory, so DRAM is idle; the barrier per round, not a
-        # unit's throughput, sets the time.  Reported against the 32-bit ALU peak.
-        ops = 8.0 * n_unique * K
+        # k-means++ in one thread-block cluster of 16 CTAs: K dependent rounds, each
+        # refreshing the exact integer D^2 of every unique colour (5 integer operations:
+        # dp4a distance, two norm terms, minimum, weighted sum) and drawing the next
+        # centre through two cross-CTA exchanges (every warp's total pushed to every CTA,
+        # then the sampled key pushed back by the CTA holding it).  The colours live in
+        # registers, so DRAM is idle; the exchanges' latency sets the round time.
+        ops = 5.0 * n_unique * K
         achieved = ops / (stage_mean[1] * 1e-3) / 1e12
-        alu_peak = fp32_peak / 2.0  # one integer operation per lane per clock
-        roof = {"kernel": "seed_far_cluster (kq_seed, k-means++: 16-CTA cluster, one barrier per round)",
+        cl = 16
+        roof = {"kernel": "seed_far_cluster (kq_seed, k-means++: one 16-CTA cluster, st.async/mbarrier exchanges)",
                 "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
-                "frac": achieved / alu_peak, "traffic": 818432,
+                "frac": achieved / alu_peak, "traffic": None,
                 "peak_source": "derived: %d SMs x 128 lanes x 1 op x %.0f MHz (max SM clock, measured)"
                                % (props.multi_processor_count, sm_max),
-                "algorithmic": "8 integer ops per unique colour per round x %d rounds (latency-bound: "
-                               "cluster barrier per round)" % K,
-                "traffic_source": "profiles/seed_far_cluster_lloyd_kernel_paper512_k256.txt (dram read+write "
-                                  "per launch)"}
+                "algorithmic": "5 integer ops per unique colour per round x %d rounds" % K,
+                "frac_of_cluster_sms": achieved / (alu_peak * cl / props.multi_processor_count),
+                "latency": {"us_per_round": 1e3 * stage_mean[1] / K, "rounds": K,
+                            "exchanges_per_round": 2,
+                            "note": "latency-bound: per round one push of every warp total to every CTA, one "
+                                    "push of the sampled key; the cluster's 16 SMs idle between them"},
+                "traffic_note": "DRAM traffic per launch: see profiles/seed_far_cluster_paper512_k256.txt"}
     else:
         byts = (3.0 * n + 8.0 * n_unique) if dom == 0 else (4.0 * n + 8.0 * n_unique)
         achieved = byts / (stage_mean[dom] * 1e-3) / 1e9
         roof = {"kernel": names[dom], "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": None, "peak_source": "MEASURED_PEAKS hbm_gbs",
+                "frac": achieved / hbm_peak, "traffic": None, "peak_source": hbm_source,
                 "algorithmic": "pixels 3 B in (+1 B out) + 8 B per unique colour"}
 
     # ---- the other kernels against their own rooflines (after the timed region)
@@ -844,6 +1095,13 @@ def run_gpu(args, rank, world, local) -> None:
             "stages_ms": dict(zip(names, stage_mean)),
             "kernels": kernels,
             "wall_s_timed_region": wall, "clock_samples": clk["samples"]}
+    if rank == 0 and world == 1 and args.workload == WORKLOAD and not args.no_extras:
+        big, (sub, bimgs), (pool, simgs) = extra_inputs()
+        line["extras"] = {"large_4096": extra_large(big, K, dev, fp32_peak, hbm_peak, alu_peak),
+                          "batched_subset": extra_batched(sub, bimgs, dev),
+                          "serving_short": extra_serving(pool, simgs, dev),
+                          "peaks": {"hbm_gbs": hbm_peak, "hbm_source": hbm_source, "fp32_tflops": fp32_peak,
+                                    "alu_tops": alu_peak}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(img, K, wl.eps, wl.max_iter)
     if rank == 0:

@@ -131,8 +131,7 @@ KQ_API int kq_histogram(const uint8_t *rgb, int64_t n_pixels, uint32_t *keys, ui
  * stride = 1 is the whole image.
  *   rgb        height rows of width x 3 bytes; row y starts at rgb + y * pitch.
  *   pitch      bytes between rows, >= 3 * width.
- * Other arguments and results as kq_histogram.  Note that kq_map needs the
- * histogram of every pixel it maps (kq_histogram of the whole image).
+ * Other arguments and results as kq_histogram.
  */
 KQ_API int kq_histogram_strided(const uint8_t *rgb, int32_t height, int32_t width, int64_t pitch, int32_t stride,
                                 uint32_t *keys, uint32_t *weights, int32_t capacity, int32_t *n_unique, void *ws,
@@ -186,16 +185,17 @@ KQ_API int kq_lloyd(const uint32_t *keys, const uint32_t *weights, const int32_t
 /*
  * Pixel mapping (Section 1; Section 2.1 notes that k-means maps by a full
  * palette search): idx[i] = argmin_k |rgb_i - palette_k|^2 in exact integer
- * arithmetic, lowest index on ties.
- *   keys, weights, n_unique   kq_histogram's output for THIS image (each unique
- *              colour is matched once, then every pixel looks its colour up).
- *   palette    K x 3 bytes.   idx   out: n_pixels bytes.
- *   sse_num    out (device int64, nullable): sum over pixels of the squared
+ * arithmetic, lowest index on ties.  The search per pixel is exact but visits
+ * only the palette entries that can be nearest somewhere in the pixel's cell of
+ * 8 x 8 x 8 colours (found from the palette alone at the start of the call).
+ *   rgb        n_pixels x 3 bytes, packed HWC, any alignment.
+ *   palette    K x 3 bytes (device).   idx   out: n_pixels bytes.
+ *   sse_num    out (device int64, nullable): sum over the pixels of the squared
  *              error, the numerator of the MSE of Section 3.1 (Eq. 2).
+ * Needs no histogram and keeps no state between calls.
  */
-KQ_API int kq_map(const uint8_t *rgb, int64_t n_pixels, const uint32_t *keys, const uint32_t *weights,
-           const int32_t *n_unique, const uint8_t *palette, int32_t K, uint8_t *idx, int64_t *sse_num, void *ws,
-           size_t ws_bytes, kq_stream_t stream);
+KQ_API int kq_map(const uint8_t *rgb, int64_t n_pixels, const uint8_t *palette, int32_t K, uint8_t *idx,
+                  int64_t *sse_num, void *ws, size_t ws_bytes, kq_stream_t stream);
 
 /* ------------------------------------------------------------------ batches
  * Many images of uneven size and K in one persistent launch (the paper treats
@@ -349,6 +349,11 @@ KQ_API int kq_pixel_keys(const uint8_t *rgb, int64_t n_pixels, uint32_t *keys, u
  */
 KQ_API int kq_set_wait_limit(void *ws, size_t ws_bytes, uint32_t wait_limit_us, uint32_t missing_arrivals,
                              kq_stream_t stream);
+
+/* Distance calculations of the last kq_map on `ws` (the paper's NDC for the
+ * mapping step: palette entries examined, summed over the pixels), copied to
+ * *h_ndc (synchronizes `stream`). */
+KQ_API int kq_map_ndc_read(const void *ws, int64_t *h_ndc, kq_stream_t stream);
 
 /* Device status word of `ws` copied to *h_status (synchronizes `stream`). */
 KQ_API int kq_status_read(const void *ws, int32_t *h_status, kq_stream_t stream);

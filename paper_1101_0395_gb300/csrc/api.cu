@@ -146,17 +146,15 @@ int kq_lloyd(const uint32_t *keys, const uint32_t *weights, const int32_t *n_uni
                             sse_hist, ws, L, (cudaStream_t)stream, 0);
 }
 
-int kq_map(const uint8_t *rgb, int64_t n_pixels, const uint32_t *keys, const uint32_t *weights,
-           const int32_t *n_unique, const uint8_t *palette, int32_t K, uint8_t *idx, int64_t *sse_num, void *ws,
-           size_t ws_bytes, kq_stream_t stream)
+int kq_map(const uint8_t *rgb, int64_t n_pixels, const uint8_t *palette, int32_t K, uint8_t *idx, int64_t *sse_num,
+           void *ws, size_t ws_bytes, kq_stream_t stream)
 {
     Layout L;
     if (!ws_ok(ws, ws_bytes, &L)) return KQ_EINVAL;
-    if (n_pixels < 0 || !keys || !weights || !n_unique || !palette) return KQ_EINVAL;
+    if (n_pixels < 0 || !palette) return KQ_EINVAL;
     if (n_pixels > 0 && (!rgb || !idx)) return KQ_EINVAL;
     if (K < 1 || K > kq::kMaxK) return KQ_EINVAL;
-    return kq::launch_map(rgb, n_pixels, keys, weights, n_unique, palette, K, idx, sse_num, ws, L,
-                          (cudaStream_t)stream);
+    return kq::launch_map(rgb, n_pixels, palette, K, idx, sse_num, ws, L, (cudaStream_t)stream);
 }
 
 int kq_pixel_keys(const uint8_t *rgb, int64_t n_pixels, uint32_t *keys, uint32_t *weights, int32_t *n_out,
@@ -186,6 +184,18 @@ int kq_status_read(const void *ws, int32_t *h_status, kq_stream_t stream)
         return KQ_ECUDA;
     if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return KQ_ECUDA;
     *h_status = v;
+    return KQ_OK;
+}
+
+int kq_map_ndc_read(const void *ws, int64_t *h_ndc, kq_stream_t stream)
+{
+    if (!ws || !h_ndc) return KQ_EINVAL;
+    const kq::Ctl *ctl = reinterpret_cast<const kq::Ctl *>(ws);
+    unsigned long long v = 0;
+    if (cudaMemcpyAsync(&v, &ctl->map_ndc, sizeof(v), cudaMemcpyDeviceToHost, (cudaStream_t)stream) != cudaSuccess)
+        return KQ_ECUDA;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return KQ_ECUDA;
+    *h_ndc = (int64_t)v;
     return KQ_OK;
 }
 

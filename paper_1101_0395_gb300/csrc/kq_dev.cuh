@@ -23,6 +23,7 @@ constexpr int kHistChunks = kBitWords / kHistChunkWords;  // 2048
 constexpr int kMaxGrid = 4096;             // upper bound on persistent grid sizes
 constexpr int kSeedChunks = 512;           // chunks of the unique list for VAR / DEN lookups
 constexpr int kDenCells = 64;              // 4 levels per channel
+constexpr int kMapCells = 32 * 32 * 32;    // kq_map's cells: 8^3 colours each
 constexpr uint64_t kWaitNs = 4000000000ull;  // device-side wait limit (4 s)
 constexpr int kWuCells = 32 * 32 * 32;     // Wu's grid: 5 bits per channel
 constexpr int kWuCum = 33 * 33 * 33;       // cumulative moments with a zero border
@@ -47,14 +48,15 @@ struct Ctl {
     unsigned long long var_w;  // sum of weights
     unsigned long long var_s1[3];
     unsigned long long var_s2[3];
-    uint32_t pad3[18];
+    unsigned long long map_ndc;  // distance calculations of the last kq_map (candidates over all pixels)
+    uint32_t pad3[16];
 };
 static_assert(sizeof(Ctl) <= 4096, "control block must fit its region");
 static_assert(offsetof(Ctl, bar_count) == 128, "the barrier counter has its own 128-byte line");
 
 // ---------------------------------------------------------------- workspace layout
 struct Layout {
-    size_t ctl, hist_cnt, hist_bits, hist_chunk, lut;
+    size_t ctl, hist_cnt, hist_bits, hist_chunk, m_desc, m_list;
     size_t l_sums, l_sse, l_rows, l_cent;
     size_t s_d2, s_part, s_slot, s_chunk, s_gcnt, s_misc, s_labels, s_centers, s_wu, s_gpart;
     size_t total;
@@ -82,7 +84,8 @@ __host__ __device__ inline Layout layout_for(int64_t max_unique)
     L.hist_cnt = take(sizeof(uint32_t) * (size_t)kKeySpace);
     L.hist_bits = take(sizeof(uint32_t) * (size_t)kBitWords);
     L.hist_chunk = take(sizeof(uint32_t) * 2 * (size_t)kHistChunks);  // totals, then bases
-    L.lut = take((size_t)kKeySpace);
+    L.m_desc = take(sizeof(unsigned long long) * (size_t)kMapCells);
+    L.m_list = take((size_t)kMapCells * kMaxK);
     L.l_sums = take(sizeof(unsigned long long) * 3 * kMaxK * 4);
     L.l_sse = take(sizeof(double) * 2 * kMaxGrid);
     L.l_rows = take(sizeof(uint32_t) * kMaxK * kMaxK);
@@ -369,7 +372,6 @@ int launch_histogram_strided(const uint8_t *rgb, int32_t h, int32_t w, int64_t p
                              cudaStream_t s);
 int launch_pixel_keys(const uint8_t *rgb, int64_t n, uint32_t *keys, uint32_t *weights, int32_t *n_out,
                       cudaStream_t s);
-int launch_map(const uint8_t *rgb, int64_t n, const uint32_t *keys, const uint32_t *w, const int32_t *n_unique,
-               const uint8_t *palette, int K, uint8_t *idx, int64_t *sse_num, void *ws, const Layout &L,
-               cudaStream_t s);
+int launch_map(const uint8_t *rgb, int64_t n, const uint8_t *palette, int K, uint8_t *idx, int64_t *sse_num,
+               void *ws, const Layout &L, cudaStream_t s);
 }  // namespace kq

@@ -509,33 +509,53 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long x)
     return x;
 }
 
-// Sum (k-means++) or maximum (minmax) per CTA of the C x 16 pushed warp values:
-// lane l covers CTA l / (32 / C) and C / 2 of its warps; the result for CTA c is
-// returned in lane c (lanes >= C get copies).
-template <bool KPP>
-__device__ __forceinline__ unsigned long long cta_values(const ClusterShared &sh, int b, int C, int lane)
+// Which pushed warp values lane `lane` combines in cta_values (computed once per
+// kernel: C is 8 or 16, so lanes_per_cta = 32 / C is 4 or 2).
+struct CtaLanes {
+    int row;   // CTA whose values this lane reads
+    int col;   // first of its warps
+    int per;   // warps per lane: 16 / lanes_per_cta
+    int lpc;   // lanes per CTA
+    int from;  // lane holding CTA (lane % C)'s result
+};
+
+__device__ __forceinline__ CtaLanes cta_lanes(int C, int lane)
 {
-    const int lpc = 32 / C;  // lanes per CTA: 2 or 4
-    const int c = lane / lpc, part = lane % lpc, per = kClWarps / lpc;
-    const unsigned long long *row = &sh.wtot[b][c][part * per];
-    unsigned long long s = 0ull;
+    const int sh = C == 16 ? 1 : 2;
+    CtaLanes L;
+    L.lpc = 1 << sh;
+    L.row = lane >> sh;
+    L.per = kClWarps >> sh;
+    L.col = (lane & (L.lpc - 1)) * L.per;
+    L.from = (lane & (C - 1)) << sh;
+    return L;
+}
+
+// Sum (k-means++) or maximum (minmax) per CTA of the C x 16 pushed warp values: the
+// lanes of CTA c each combine `per` of its warps (a two-level tree), then the
+// lanes_per_cta partial results are combined; the result for CTA c is returned in
+// lane c (lanes >= C get copies).
+template <bool KPP>
+__device__ __forceinline__ unsigned long long cta_values(const ClusterShared &sh, int b, const CtaLanes &L)
+{
+    const unsigned long long *row = &sh.wtot[b][L.row][L.col];
+    unsigned long long v[kClWarps / 2];
 #pragma unroll
-    for (int q = 0; q < kClWarps / 2; ++q) {
-        if (q < per) {
-            const unsigned long long v = row[q];
-            if (KPP) s += v;
-            else s = v > s ? v : s;
-        }
+    for (int q = 0; q < kClWarps / 2; ++q) v[q] = q < L.per ? row[q] : 0ull;
+#pragma unroll
+    for (int w = kClWarps / 4; w; w >>= 1) {
+#pragma unroll
+        for (int q = 0; q < w; ++q) v[q] = KPP ? v[q] + v[q + w] : (v[q + w] > v[q] ? v[q + w] : v[q]);
     }
+    unsigned long long s = v[0];
 #pragma unroll
     for (int o = 1; o < 4; o <<= 1) {
-        if (o < lpc) {
+        if (o < L.lpc) {
             const unsigned long long y = __shfl_down_sync(kFull, s, o);
-            if (KPP) s += y;
-            else s = y > s ? y : s;
+            s = KPP ? s + y : (y > s ? y : s);
         }
     }
-    return __shfl_sync(kFull, s, (lane % C) * lpc);
+    return __shfl_sync(kFull, s, L.from);
 }
 
 // The K rounds of one CTA whose threads hold EPT or EPT - 1 colours each.  The CTA's
@@ -601,10 +621,13 @@ __device__ __forceinline__ void cluster_rounds(const ClusterArgs &a, ClusterShar
     // every CTA's barriers exist and are armed before anyone pushes
     cluster_sync_all();
 
+    const CtaLanes lanes = cta_lanes(C, lane);
     uint32_t ckey = 0u, cnorm = 0u;
     for (int r = 0; r < K; ++r) {
         const int b = r & 1;
         const uint32_t ph = (uint32_t)(r >> 1) & 1u;
+        uint64_t u = 0;
+        if (warp == 0) u = KPP ? rand64(a.seed, 2, (uint32_t)r) : rand64(a.seed, 3, 0);
         // ---- this thread's colours: D^2 to the newest centre; w D^2 running sums or the packed maximum
         unsigned long long acc = 0ull;
         if (r > 0) {
@@ -646,7 +669,6 @@ __device__ __forceinline__ void cluster_rounds(const ClusterArgs &a, ClusterShar
         __syncwarp();  // the lanes' shared-memory writes above precede the pushes below
         if (lane < C) push_u64(to_wtot + kWtotStride * (uint32_t)b, wv, to_data + 8u * (uint32_t)b);
         if (warp == 0) {
-            const uint64_t u = KPP ? rand64(a.seed, 2, (uint32_t)r) : rand64(a.seed, 3, 0);
             bool alive = mbar_wait(bar_data0 + 8u * (uint32_t)b, ph, a.ctl, limit_ns);
             if (tid == 0 && alive) mbar_arrive_expect(bar_data0 + 8u * (uint32_t)b, data_bytes);  // re-arm for r + 2
             if (!KPP) {
@@ -655,12 +677,15 @@ __device__ __forceinline__ void cluster_rounds(const ClusterArgs &a, ClusterShar
                 if (r == 0) {
                     next = __ldg(a.keys + below(u, (uint64_t)n));
                 } else {
-                    const unsigned long long m = warp_max_u64(cta_values<false>(sh, b, C, lane));
+                    const unsigned long long m = warp_max_u64(cta_values<false>(sh, b, lanes));
                     next = 0xFFFFFFu - (uint32_t)(m & 0xFFFFFFull);
                 }
                 if (lane == 0) sh.key[b] = next;
             } else if (alive) {
-                const unsigned long long ct = cta_values<true>(sh, b, C, lane);
+                // this CTA's own warp totals are scanned while the CTA totals are formed
+                const unsigned long long wtv = lane < kClWarps ? sh.wtot[b][rank][lane] : 0ull;
+                const unsigned long long xw = warp_incl_scan_u64<4>(wtv, lane);
+                const unsigned long long ct = cta_values<true>(sh, b, lanes);
                 const unsigned long long x = warp_incl_scan_u64<4>(lane < C ? ct : 0ull, lane);
                 const unsigned long long t = below(u, __shfl_sync(kFull, x, C - 1));
                 int g = __ffs(__ballot_sync(kFull, lane < C && x > t)) - 1;
@@ -668,8 +693,6 @@ __device__ __forceinline__ void cluster_rounds(const ClusterArgs &a, ClusterShar
                 if (g == (int)rank) {
                     // the warp of this CTA, then its thread, then the thread's colour
                     const unsigned long long r1 = t - (__shfl_sync(kFull, x, g) - __shfl_sync(kFull, ct, g));
-                    const unsigned long long wtv = lane < kClWarps ? sh.wtot[b][g][lane] : 0ull;
-                    const unsigned long long xw = warp_incl_scan_u64<4>(wtv, lane);
                     int ws = __ffs(__ballot_sync(kFull, lane < kClWarps && xw > r1)) - 1;
                     ws = ws < 0 ? 0 : ws;
                     const unsigned long long resid = r1 - (__shfl_sync(kFull, xw, ws) - __shfl_sync(kFull, wtv, ws));

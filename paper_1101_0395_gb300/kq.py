@@ -64,7 +64,7 @@ _SIGS = {
                           C.c_size_t, _vp]),
     "kq_lloyd": (C.c_int, [_vp, _vp, _vp, C.c_int32, _vp, C.c_double, C.c_int32, C.c_uint32, _vp, _vp, _vp, _vp,
                            _vp, C.c_size_t, _vp]),
-    "kq_map": (C.c_int, [_vp, C.c_int64, _vp, _vp, _vp, _vp, C.c_int32, _vp, _vp, _vp, C.c_size_t, _vp]),
+    "kq_map": (C.c_int, [_vp, C.c_int64, _vp, C.c_int32, _vp, _vp, _vp, C.c_size_t, _vp]),
     "kq_lloyd_noalloc": (C.c_int, [_vp, _vp, _vp, C.c_int32, _vp, C.c_double, C.c_int32, C.c_uint32, _vp, _vp,
                                    _vp, _vp, _vp]),
     "kq_pixel_keys": (C.c_int, [_vp, C.c_int64, _vp, _vp, _vp, _vp]),
@@ -73,6 +73,7 @@ _SIGS = {
     "kq_status_read": (C.c_int, [_vp, C.POINTER(C.c_int32), _vp]),
     "kq_status_clear": (C.c_int, [_vp, _vp]),
     "kq_set_wait_limit": (C.c_int, [_vp, C.c_size_t, C.c_uint32, C.c_uint32, _vp]),
+    "kq_map_ndc_read": (C.c_int, [_vp, C.POINTER(C.c_int64), _vp]),
     "kq_strerror": (C.c_char_p, [C.c_int]),
     "kq_batch_scratch_bytes": (C.c_size_t, [C.c_int32]),
     "kq_batch_workspace_size": (C.c_size_t, []),
@@ -175,18 +176,22 @@ def kq_lloyd_noalloc(keys: torch.Tensor, weights: torch.Tensor, n_unique: torch.
                                                       _stream(stream)))
 
 
-def kq_map(rgb: torch.Tensor, keys: torch.Tensor, weights: torch.Tensor, n_unique: torch.Tensor,
-           palette: torch.Tensor, K: int, idx: torch.Tensor, ws: torch.Tensor,
+def kq_map(rgb: torch.Tensor, palette: torch.Tensor, K: int, idx: torch.Tensor, ws: torch.Tensor,
            sse_num: Optional[torch.Tensor] = None, n_pixels: Optional[int] = None, stream=None) -> None:
     n = rgb.numel() // 3 if n_pixels is None else int(n_pixels)
-    _check("kq_map", lib().kq_map(_ptr(rgb) if n else None, n, _ptr(keys), _ptr(weights), _ptr(n_unique),
-                                  _ptr(palette), int(K), _ptr(idx) if n else None, _ptr(sse_num), _ptr(ws),
-                                  ws.numel() * ws.element_size(), _stream(stream)))
+    _check("kq_map", lib().kq_map(_ptr(rgb) if n else None, n, _ptr(palette), int(K), _ptr(idx) if n else None,
+                                  _ptr(sse_num), _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)))
 
 
 def kq_status_read(ws: torch.Tensor, stream=None) -> int:
     v = C.c_int32(0)
     _check("kq_status_read", lib().kq_status_read(_ptr(ws), C.byref(v), _stream(stream)))
+    return int(v.value)
+
+
+def kq_map_ndc_read(ws: torch.Tensor, stream=None) -> int:
+    v = C.c_int64(0)
+    _check("kq_map_ndc_read", lib().kq_map_ndc_read(_ptr(ws), C.byref(v), _stream(stream)))
     return int(v.value)
 
 
@@ -276,7 +281,7 @@ class Quantizer:
         kq_lloyd(self.keys, self.weights, self.n_unique, K, c, eps, max_iter, self.labels, pal, self.ws,
                  stats=self.stats, flags=flags, stream=stream)
         idx = self.idx[:n]
-        kq_map(rgb, self.keys, self.weights, self.n_unique, pal, K, idx, self.ws, sse_num=self.sse_num,
+        kq_map(rgb, pal, K, idx, self.ws, sse_num=self.sse_num,
                stream=stream)
         self.launches += (launches("kq_histogram", n) + launches("kq_seed", n, scheme, K) + launches("kq_lloyd")
                           + launches("kq_map", n))

@@ -80,7 +80,7 @@ class Run:
         out = torch.zeros(self.n + 64, dtype=torch.uint8, device="cuda")
         idx = out[idx_offset:idx_offset + self.n]
         sse = torch.zeros(1, dtype=torch.int64, device="cuda")
-        kq.kq_map(self.rgb if rgb is None else rgb, self.keys, self.weights, self.n_unique, pal, K, idx, self.ws,
+        kq.kq_map(self.rgb if rgb is None else rgb, pal, K, idx, self.ws,
                   sse_num=sse, n_pixels=self.n)
         torch.cuda.synchronize()
         return idx.cpu().numpy(), int(sse.item())

@@ -17,7 +17,7 @@ def test_exports_every_declared_symbol():
                           "kq_lloyd_noalloc", "kq_status_read", "kq_status_clear", "kq_strerror",
                           "kq_batch_scratch_bytes", "kq_batch_workspace_size", "kq_batch_max_cluster",
                           "kq_batch_plan", "kq_batch_run", "kq_batch_tune", "kq_pixel_keys",
-                          "kq_histogram_strided", "kq_set_wait_limit"}
+                          "kq_histogram_strided", "kq_set_wait_limit", "kq_map_ndc_read"}
     L = kq.lib()
     for n in names:
         assert getattr(L, n) is not None
@@ -26,7 +26,7 @@ def test_exports_every_declared_symbol():
 def test_workspace_size():
     small = kq.kq_workspace_size(1, 256)
     big = kq.kq_workspace_size(4096 * 4096, 256)
-    assert small > (64 << 20) + (16 << 20)  # direct colour tables + lookup table
+    assert small > (64 << 20) + (2 << 20)  # direct colour counters + presence bitmap
     assert big - small >= 9 * (4096 * 4096 - 1) - 1024  # 9 bytes per possible unique colour
     assert kq.kq_workspace_size(1 << 30, 256) == kq.kq_workspace_size(1 << 24, 256)  # N' <= 2^24
     assert kq.kq_workspace_size(-1, 256) == 0 and kq.kq_workspace_size(10, 0) == 0
@@ -47,7 +47,7 @@ def test_invalid_arguments_are_rejected_synchronously():
     for K in (0, 257):
         assert L.kq_seed(p, p, p, K, 0, 1, None, p, WS, size, None) == kq.KQ_EINVAL
         assert L.kq_lloyd(p, p, p, K, p, 1e-4, 10, 0, p, p, None, None, WS, size, None) == kq.KQ_EINVAL
-        assert L.kq_map(p, 10, p, p, p, p, K, p, None, WS, size, None) == kq.KQ_EINVAL
+        assert L.kq_map(p, 10, p, K, p, None, WS, size, None) == kq.KQ_EINVAL
     assert L.kq_seed(p, p, p, 8, 7, 1, None, p, WS, size, None) == kq.KQ_EINVAL  # USER is not a seeding scheme
     assert L.kq_seed(p, p, p, 8, -1, 1, None, p, WS, size, None) == kq.KQ_EINVAL
     assert L.kq_seed(p, p, p, 8, 9, 1, None, p, WS, size, None) == kq.KQ_EINVAL
@@ -57,9 +57,11 @@ def test_invalid_arguments_are_rejected_synchronously():
     assert L.kq_lloyd(p, p, p, 8, p, 1e-4, 10, 4, p, p, None, None, WS, size, None) == kq.KQ_EINVAL
     assert L.kq_lloyd(p, p, p, 8, p, float("nan"), 10, 0, p, p, None, None, WS, size, None) == kq.KQ_EINVAL
     assert L.kq_lloyd(None, p, p, 8, p, 1e-4, 10, 0, p, p, None, None, WS, size, None) == kq.KQ_EINVAL
-    assert L.kq_map(p, 10, p, p, p, p, 8, None, None, WS, size, None) == kq.KQ_EINVAL
+    assert L.kq_map(p, 10, p, 8, None, None, WS, size, None) == kq.KQ_EINVAL
+    assert L.kq_map(p, 10, None, 8, p, None, WS, size, None) == kq.KQ_EINVAL
     assert L.kq_status_read(None, None, None) == kq.KQ_EINVAL
     assert L.kq_set_wait_limit(None, size, 1000, 1, None) == kq.KQ_EINVAL
+    assert L.kq_map_ndc_read(None, None, None) == kq.KQ_EINVAL
     assert L.kq_set_wait_limit(WS, 4096, 1000, 1, None) == kq.KQ_EINVAL
     assert L.kq_workspace_init(None, size, None) == kq.KQ_EINVAL
 

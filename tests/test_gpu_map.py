@@ -85,3 +85,54 @@ def test_map_large_sampled():
     uidx, _ = oracle.map_pixels(uimg, pal)
     d = ((oracle.key_to_rgb(keys) - pal[uidx].astype(np.int64)) ** 2).sum(axis=1)
     assert sse == int((d * w.astype(np.int64)).sum())
+
+
+def test_map_needs_no_histogram_and_keeps_no_state():
+    # kq_map depends on the pixels and the palette only: two images mapped in turn on
+    # one workspace, with no histogram computed, each equal to the oracle's mapping
+    from paper_1101_0395_gb300 import kq
+
+    a = synth.WORKLOADS["plain_256"].make(0)
+    b = synth.WORKLOADS["paper_512"].make(1)
+    ws = torch.zeros(kq.kq_workspace_size(b.size // 3, 256), dtype=torch.uint8, device="cuda")
+    for K, seed in ((64, 5), (200, 6)):
+        pal = palette_for(None, K, seed)
+        for img in (a, b, a):
+            r = Run(img, ws=ws)
+            idx, sse = r.map(pal)
+            oidx, osse = oracle.map_pixels(img, pal)
+            assert np.array_equal(idx, oidx) and sse == osse
+    assert kq.kq_status_read(ws) == kq.KQ_OK
+
+
+@pytest.mark.parametrize("K", [1, 2, 16, 256])
+def test_map_pruned_search_counts(K):
+    # the palette search is exact and prunes: N <= NDC <= N K
+    from paper_1101_0395_gb300 import kq
+
+    img = synth.WORKLOADS["paper_512"].make(2)
+    r = Run(img)
+    keys, w = r.histogram()
+    pal = palette_for(keys, K, 3 * K)
+    idx, sse = r.map(pal)
+    oidx, osse = oracle.map_pixels(img, pal)
+    assert np.array_equal(idx, oidx) and sse == osse
+    ndc = kq.kq_map_ndc_read(r.ws)
+    n = img.size // 3
+    assert n <= ndc <= n * K
+    if K == 256:
+        assert ndc < n * K // 16
+
+
+def test_map_duplicate_and_clustered_palettes():
+    # palettes with repeated entries and entries closer together than the colours
+    img = synth.WORKLOADS["plain_256"].make(2)
+    r = Run(img)
+    keys, w = r.histogram()
+    rng = np.random.default_rng(77)
+    base = rng.integers(0, 256, size=(8, 3))
+    pal = np.concatenate([base, base, base + rng.integers(-2, 3, size=(8, 3))]).clip(0, 255).astype(np.uint8)
+    rng.shuffle(pal)
+    idx, sse = r.map(pal)
+    oidx, osse = oracle.map_pixels(img, pal)
+    assert np.array_equal(idx, oidx) and sse == osse
