@@ -249,3 +249,4 @@ def test_large_image_lockstep():
     assert np.array_equal(a["centers"], b["centers"])
     assert np.array_equal(a["sse_hist"], b["sse_hist"])
     assert a["stats"]["ndc"] < b["stats"]["ndc"] == 256 * keys.size * 12
+

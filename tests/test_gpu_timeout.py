@@ -1,7 +1,9 @@
 """Failure detection on the device without a GPU fault.
 
-kq_set_wait_limit gives the bounded waits of the kernels a 1 ms limit and makes
-them expect one arrival that never comes (no block is missing in fact: the
+kq_set_wait_limit gives the bounded waits of the kernels (the grid barriers of
+the whole-grid Lloyd and k-means++ launches, the mbarrier exchanges of the
+cluster k-means++) a 1 ms limit and makes them expect one arrival that never
+comes (no block is missing in fact: the
 count is raised on the host).  Every wait then runs out: the kernel writes
 KQ_ETIMEOUT to the workspace's status word (and to kq_lloyd's statistics),
 the other waiters give up in turn, and the launch returns.  After
@@ -28,8 +30,20 @@ def paper():
     return r, keys, w
 
 
-def test_lloyd_grid_barrier_times_out_and_recovers(paper):
-    r, keys, w = paper
+@pytest.fixture(scope="module")
+def many():
+    # ~377k unique colours: Lloyd and k-means++ run on the whole grid (grid barriers)
+    require_cuda()
+    rng = np.random.default_rng(20110)
+    img = rng.integers(0, 256, size=(600, 640, 3), dtype=np.uint8)
+    r = Run(img)
+    keys, w = r.histogram()
+    assert keys.size > (1 << 17)
+    return r, keys, w
+
+
+def test_lloyd_grid_barrier_times_out_and_recovers(many):
+    r, keys, w = many
     c0, _ = oracle.seed(keys, w, 64, "KPP", 3)
     want = r.lloyd(c0, eps=1e-4, max_iter=100)
     kq.kq_set_wait_limit(r.ws, LIMIT_US, missing_arrivals=1)
@@ -60,13 +74,9 @@ def test_cluster_seeding_exchange_times_out_and_recovers(paper, scheme):
     assert np.array_equal(got, want)
 
 
-def test_grid_seeding_barrier_times_out_and_recovers():
-    # N' ~ 360k unique colours: above one cluster, k-means++ runs on the whole grid
-    require_cuda()
-    rng = np.random.default_rng(20110)
-    img = rng.integers(0, 256, size=(600, 640, 3), dtype=np.uint8)
-    r = Run(img)
-    keys, w = r.histogram()
+def test_grid_seeding_barrier_times_out_and_recovers(many):
+    # above one cluster's capacity, k-means++ runs on the whole grid
+    r, keys, w = many
     assert keys.size > 16 * 11264
     want, _ = oracle.seed(keys, w, 16, "KPP", 5)
     kq.kq_set_wait_limit(r.ws, LIMIT_US, missing_arrivals=1)
@@ -78,9 +88,9 @@ def test_grid_seeding_barrier_times_out_and_recovers():
     assert np.array_equal(got, want)
 
 
-def test_limit_alone_changes_nothing(paper):
+def test_limit_alone_changes_nothing(many):
     # a limit far above the run time, no missing arrival: normal results
-    r, keys, w = paper
+    r, keys, w = many
     c0, _ = oracle.seed(keys, w, 16, "FGY", 1)
     want = r.lloyd(c0, eps=1e-4, max_iter=50)
     kq.kq_set_wait_limit(r.ws, 2_000_000, missing_arrivals=0)
