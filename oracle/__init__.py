@@ -17,6 +17,10 @@ Functions and the passage each follows:
   mse, psnr   -- Section 3.1, Eqs. 2 and 3
   seed        -- Section 2.3 generic initialization schemes, and WU (Section 3.3)
   wu          -- Wu's greedy orthogonal bipartitioning (Section 3.3, WSM-WU)
+  lab, lab_points, lab_palette -- the CIE L*a*b* space of Section 2.1 (sRGB,
+                 D65; fixed-point points) and its inverse to an sRGB palette
+  assign_points, update_points, lloyd_points, seed_points_fgy -- Algorithm 2
+                 and Forgy seeding on fixed-point 3-D points (L*a*b*)
 
 Parity status: every function above is pinned by ``tests/test_oracle_pins.py``
 (closed forms, brute force on tiny inputs, invariants, library routines).
@@ -103,6 +107,22 @@ def lib() -> C.CDLL:
         L.or_var_channel.argtypes = [_u32p, _u32p, C.c_int64]
         L.or_wu.restype = C.c_int
         L.or_wu.argtypes = [_u32p, _u32p, C.c_int64, C.c_int, _f64p]
+        _i32p = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+        L.or_lab.restype = None
+        L.or_lab.argtypes = [C.c_uint32, _f64p]
+        L.or_lab_points.restype = None
+        L.or_lab_points.argtypes = [_u32p, C.c_int64, _i32p]
+        L.or_lab_palette.restype = None
+        L.or_lab_palette.argtypes = [_f64p, C.c_int, _u8p]
+        L.or_assign_points.restype = C.c_double
+        L.or_assign_points.argtypes = [_i32p, _u32p, C.c_int64, C.c_int, _f64p, _u8p, _opt(_f64p), _opt(_f64p)]
+        L.or_update_points.restype = None
+        L.or_update_points.argtypes = [_i32p, _u32p, C.c_int64, C.c_int, _u8p, _f64p, _f64p, _opt(_i64p)]
+        L.or_lloyd_points.restype = C.c_int
+        L.or_lloyd_points.argtypes = [_i32p, _u32p, C.c_int64, C.c_int, _f64p, C.c_double, C.c_int, _u8p,
+                                      _opt(_f64p), C.POINTER(C.c_int), _opt(_i64p)]
+        L.or_seed_points_fgy.restype = None
+        L.or_seed_points_fgy.argtypes = [_i32p, C.c_int64, C.c_int, C.c_uint64, _f64p]
         L.or_den_quota.restype = None
         L.or_den_quota.argtypes = [_i64p, _i64p, C.c_int, _i64p]
         _libs[_variant] = L
@@ -241,6 +261,81 @@ def wu(keys: np.ndarray, w: np.ndarray, K: int) -> Tuple[np.ndarray, int]:
     if nb < 0:
         raise ValueError("oracle wu failed")
     return c.reshape(K, 3), int(nb)
+
+
+LAB_SCALE = 256  # fixed-point units per L*a*b* unit
+
+
+def lab(keys: np.ndarray) -> np.ndarray:
+    """CIE 1976 L*a*b* (D65) of 24-bit sRGB colours, FP64, (n, 3)."""
+    keys = np.ascontiguousarray(keys, dtype=np.uint32).reshape(-1)
+    out = np.empty((keys.size, 3), dtype=np.float64)
+    v = np.empty(3, dtype=np.float64)
+    for i, k in enumerate(keys):
+        lib().or_lab(int(k), v)
+        out[i] = v
+    return out
+
+
+def lab_points(keys: np.ndarray) -> np.ndarray:
+    """Fixed-point L*a*b* points (n, 4) int32: round(L*, a*, b* x 256), 0."""
+    keys = np.ascontiguousarray(keys, dtype=np.uint32).reshape(-1)
+    pts = np.empty((max(keys.size, 1), 4), dtype=np.int32)
+    lib().or_lab_points(keys, keys.size, pts)
+    return pts[:keys.size]
+
+
+def lab_palette(centers: np.ndarray) -> np.ndarray:
+    """sRGB palette (K, 3) uint8 of centres given in fixed-point L*a*b* units."""
+    c = np.ascontiguousarray(centers, dtype=np.float64).reshape(-1)
+    pal = np.empty(c.size, dtype=np.uint8)
+    lib().or_lab_palette(c, c.size // 3, pal)
+    return pal.reshape(-1, 3)
+
+
+def assign_points(pts: np.ndarray, w: np.ndarray, centers: np.ndarray):
+    pts = np.ascontiguousarray(pts, dtype=np.int32)
+    w = np.ascontiguousarray(w, dtype=np.uint32)
+    c = np.ascontiguousarray(centers, dtype=np.float64).reshape(-1)
+    n = pts.shape[0]
+    lab_ = np.empty(max(n, 1), dtype=np.uint8)
+    d1 = np.empty(max(n, 1), dtype=np.float64)
+    d2 = np.empty(max(n, 1), dtype=np.float64)
+    sse = lib().or_assign_points(pts, w, n, c.size // 3, c, lab_, d1, d2)
+    return lab_[:n], d1[:n], d2[:n], sse
+
+
+def update_points(pts: np.ndarray, w: np.ndarray, labels: np.ndarray, centers: np.ndarray):
+    pts = np.ascontiguousarray(pts, dtype=np.int32)
+    w = np.ascontiguousarray(w, dtype=np.uint32)
+    c = np.ascontiguousarray(centers, dtype=np.float64).reshape(-1)
+    K = c.size // 3
+    out = np.empty_like(c)
+    sums = np.empty(K * 4, dtype=np.int64)
+    lib().or_update_points(pts, w, pts.shape[0], K, np.ascontiguousarray(labels, dtype=np.uint8), c, out, sums)
+    return out.reshape(K, 3), sums.reshape(K, 4)
+
+
+def lloyd_points(pts: np.ndarray, w: np.ndarray, centers: np.ndarray, eps: float, max_iter: int) -> Dict:
+    pts = np.ascontiguousarray(pts, dtype=np.int32)
+    w = np.ascontiguousarray(w, dtype=np.uint32)
+    c = np.array(centers, dtype=np.float64).reshape(-1).copy()
+    K = c.size // 3
+    lab_ = np.zeros(max(pts.shape[0], 1), dtype=np.uint8)
+    hist = np.zeros(max(1, max_iter), dtype=np.float64)
+    conv = C.c_int(0)
+    sums = np.zeros(K * 4, dtype=np.int64)
+    it = lib().or_lloyd_points(pts, w, pts.shape[0], K, c, float(eps), int(max_iter), lab_, hist, C.byref(conv),
+                               sums)
+    return {"centers": c.reshape(K, 3), "labels": lab_[:pts.shape[0]], "sse_hist": hist[:it], "iters": it,
+            "converged": bool(conv.value), "sums": sums.reshape(K, 4)}
+
+
+def seed_points_fgy(pts: np.ndarray, K: int, seed_value: int) -> np.ndarray:
+    pts = np.ascontiguousarray(pts, dtype=np.int32)
+    c = np.zeros(K * 3, dtype=np.float64)
+    lib().or_seed_points_fgy(pts, pts.shape[0], int(K), seed_value & (2**64 - 1), c)
+    return c.reshape(K, 3)
 
 
 def den_quota(cellw: np.ndarray, celln: np.ndarray, K: int) -> np.ndarray:

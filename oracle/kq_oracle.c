@@ -785,3 +785,171 @@ OR_API int or_seed(const uint32_t *keys, const uint32_t *w, int64_t n, int K, in
     }
     return K;
 }
+
+/* ========================================================================= */
+/* CIE L*a*b* (Section 2.1 names L*a*b* beside RGB as a colour space for      */
+/* k-means).  An 8-bit sRGB colour (IEC 61966-2-1) is made linear, taken to   */
+/* CIE XYZ by the sRGB matrix (D65), and to CIE 1976 L*a*b* relative to the   */
+/* D65 white.  Points are kept in fixed point, OR_LAB_SCALE units per         */
+/* L*a*b* unit (rounded to nearest, ties to even), so that the weighted sums  */
+/* of a cluster stay exact integers as in RGB.                                */
+/* ========================================================================= */
+#define OR_LAB_SCALE 256.0
+
+static double srgb_linear(int v8)
+{
+    double v = (double)v8 / 255.0;
+    return v <= 0.04045 ? v / 12.92 : pow((v + 0.055) / 1.055, 2.4);
+}
+
+static double lab_f(double t)
+{
+    const double d = 6.0 / 29.0;
+    return t > d * d * d ? cbrt(t) : t / (3.0 * d * d) + 4.0 / 29.0;
+}
+
+static double lab_finv(double t)
+{
+    const double d = 6.0 / 29.0;
+    return t > d ? t * t * t : 3.0 * d * d * (t - 4.0 / 29.0);
+}
+
+/* L*, a*, b* of one 24-bit colour (FP64, every operation separately rounded). */
+OR_API void or_lab(uint32_t key, double *lab)
+{
+    int64_t r8, g8, b8;
+    key_rgb(key, &r8, &g8, &b8);
+    double r = srgb_linear((int)r8), g = srgb_linear((int)g8), b = srgb_linear((int)b8);
+    double X = (0.4124564 * r + 0.3575761 * g) + 0.1804375 * b;
+    double Y = (0.2126729 * r + 0.7151522 * g) + 0.0721750 * b;
+    double Z = (0.0193339 * r + 0.1191920 * g) + 0.9503041 * b;
+    double fx = lab_f(X / 0.95047), fy = lab_f(Y / 1.0), fz = lab_f(Z / 1.08883);
+    lab[0] = 116.0 * fy - 16.0;
+    lab[1] = 500.0 * (fx - fy);
+    lab[2] = 200.0 * (fy - fz);
+}
+
+/* Fixed-point L*a*b* points of n colours: pts[4 i + c] = rint(lab_c * 256), c < 3; pts[4 i + 3] = 0. */
+OR_API void or_lab_points(const uint32_t *keys, int64_t n, int32_t *pts)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double lab[3];
+        or_lab(keys[i], lab);
+        for (int c = 0; c < 3; ++c) pts[4 * i + c] = (int32_t)llrint(lab[c] * OR_LAB_SCALE);
+        pts[4 * i + 3] = 0;
+    }
+}
+
+/* The sRGB colour of each of K centres given in fixed-point L*a*b* units: the  */
+/* inverse of or_lab, each channel clamped to [0, 1] and rounded half up to     */
+/* 0..255.                                                                      */
+OR_API void or_lab_palette(const double *centers, int K, uint8_t *pal)
+{
+    for (int k = 0; k < K; ++k) {
+        double L = centers[3 * k] / OR_LAB_SCALE, a = centers[3 * k + 1] / OR_LAB_SCALE,
+               bb = centers[3 * k + 2] / OR_LAB_SCALE;
+        double fy = (L + 16.0) / 116.0;
+        double fx = fy + a / 500.0, fz = fy - bb / 200.0;
+        double X = 0.95047 * lab_finv(fx), Y = 1.0 * lab_finv(fy), Z = 1.08883 * lab_finv(fz);
+        double lin[3];
+        lin[0] = (3.2404542 * X - 1.5371385 * Y) - 0.4985314 * Z;
+        lin[1] = (-0.9692660 * X + 1.8760108 * Y) + 0.0415560 * Z;
+        lin[2] = (0.0556434 * X - 0.2040259 * Y) + 1.0572252 * Z;
+        for (int c = 0; c < 3; ++c) {
+            double v = lin[c];
+            v = v <= 0.0031308 ? 12.92 * v : 1.055 * pow(v, 1.0 / 2.4) - 0.055;
+            v = v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v);
+            pal[3 * k + c] = (uint8_t)floor(v * 255.0 + 0.5);
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Weighted Lloyd on fixed-point 3-D points (L*a*b* here): the steps of        */
+/* or_assign / or_update / or_lloyd with the point's three integer coordinates */
+/* in place of a colour's three bytes.  Distances in FP64, sums exact int64.   */
+/* ------------------------------------------------------------------------- */
+OR_API double or_assign_points(const int32_t *pts, const uint32_t *w, int64_t n, int K, const double *c,
+                               uint8_t *labels, double *d1, double *d2)
+{
+    double sse = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double best = INFINITY, second = INFINITY;
+        int arg = 0;
+        for (int k = 0; k < K; ++k) {
+            double dx = (double)pts[4 * i] - c[3 * k], dy = (double)pts[4 * i + 1] - c[3 * k + 1],
+                   dz = (double)pts[4 * i + 2] - c[3 * k + 2];
+            double d = dx * dx + dy * dy + dz * dz;
+            if (d < best) {
+                second = best;
+                best = d;
+                arg = k;
+            } else if (d < second) {
+                second = d;
+            }
+        }
+        labels[i] = (uint8_t)arg;
+        if (d1) d1[i] = best;
+        if (d2) d2[i] = second;
+        sse += (double)w[i] * best;
+    }
+    return sse;
+}
+
+OR_API void or_update_points(const int32_t *pts, const uint32_t *w, int64_t n, int K, const uint8_t *labels,
+                             const double *c_in, double *c_out, int64_t *sums)
+{
+    int64_t *s = (int64_t *)calloc((size_t)K * 4, sizeof(int64_t));
+    for (int64_t i = 0; i < n; ++i) {
+        int k = labels[i];
+        for (int ch = 0; ch < 3; ++ch) s[4 * k + ch] += (int64_t)w[i] * (int64_t)pts[4 * i + ch];
+        s[4 * k + 3] += (int64_t)w[i];
+    }
+    for (int k = 0; k < K; ++k) {
+        for (int ch = 0; ch < 3; ++ch)
+            c_out[3 * k + ch] = s[4 * k + 3] > 0 ? (double)s[4 * k + ch] / (double)s[4 * k + 3] : c_in[3 * k + ch];
+    }
+    if (sums) memcpy(sums, s, (size_t)K * 4 * sizeof(int64_t));
+    free(s);
+}
+
+OR_API int or_lloyd_points(const int32_t *pts, const uint32_t *w, int64_t n, int K, double *centers, double eps,
+                           int max_iter, uint8_t *labels, double *sse_hist, int *converged, int64_t *sums)
+{
+    double *next = (double *)malloc(sizeof(double) * 3 * (size_t)K);
+    double prev = 0.0;
+    int it = 0;
+    if (converged) *converged = 0;
+    while (it < max_iter) {
+        double sse = or_assign_points(pts, w, n, K, centers, labels, NULL, NULL);
+        ++it;
+        if (sse_hist) sse_hist[it - 1] = sse;
+        or_update_points(pts, w, n, K, labels, centers, next, sums);
+        memcpy(centers, next, sizeof(double) * 3 * (size_t)K);
+        if (converged_after(it, prev, sse, eps)) {
+            if (converged) *converged = 1;
+            break;
+        }
+        prev = sse;
+    }
+    free(next);
+    return it;
+}
+
+/* Forgy seeds among the points: the K indices or_seed's Forgy draws (stream 1), */
+/* each centre that point's coordinates; K >= n gives the n points in order,     */
+/* padded with copies of the last.                                               */
+OR_API void or_seed_points_fgy(const int32_t *pts, int64_t n, int K, uint64_t seed, double *c)
+{
+    if ((int64_t)K >= n) {
+        for (int k = 0; k < K; ++k)
+            for (int ch = 0; ch < 3; ++ch)
+                c[3 * k + ch] = n == 0 ? 0.0 : (double)pts[4 * (k < n ? k : n - 1) + ch];
+        return;
+    }
+    int64_t *pick = (int64_t *)malloc(sizeof(int64_t) * (size_t)K);
+    partial_shuffle(n, K, seed, 1, pick);
+    for (int k = 0; k < K; ++k)
+        for (int ch = 0; ch < 3; ++ch) c[3 * k + ch] = (double)pts[4 * pick[k] + ch];
+    free(pick);
+}

@@ -682,3 +682,106 @@ def test_wu_cannot_split_a_single_cell():
     assert nb == 1 and np.all(c == c[0])
     c2, k_eff = oracle.seed(keys, w, 5, "WU", 0)
     assert k_eff == 5 and np.array_equal(c, c2)
+
+
+# --------------------------------------------------------------------------- CIE L*a*b*
+def test_lab_reference_values():
+    # the sRGB primaries and secondaries and the mid grey, as tabulated for the
+    # standard definitions (tests/golden/lab_reference.txt)
+    for row in read_golden("lab_reference.txt"):
+        r, g, b = (int(v) for v in row[:3])
+        want = np.array([float(v) for v in row[3:]])
+        got = oracle.lab(np.array([(r << 16) | (g << 8) | b]))[0]
+        assert np.all(np.abs(got - want) <= 6e-5 + 1e-9), (row, got)
+
+
+def test_lab_closed_forms():
+    # black is the origin; white is L* = 100 with a* = b* = 0 (the matrix rows sum to
+    # the white point to 1e-7); every neutral grey has a* = b* = 0 and L* grows with
+    # the grey level; below the linear segment's end (8-bit 10: 10/255 < 0.04045) L*
+    # follows the closed form 116 (t / (3 (6/29)^2) + 4/29) - 16 = 903.3 t for Y = t
+    greys = np.arange(256, dtype=np.uint32) * 0x010101
+    lab = oracle.lab(greys)
+    assert np.array_equal(lab[0], [0.0, 0.0, 0.0])
+    assert abs(lab[255, 0] - 100.0) < 1e-4 and np.all(np.abs(lab[255, 1:]) < 1e-4)
+    assert np.all(np.abs(lab[:, 1:]) < 1e-4)
+    assert np.all(np.diff(lab[:, 0]) > 0)
+    for v in range(1, 11):
+        y = (v / 255.0) / 12.92 * (0.2126729 + 0.7151522 + 0.0721750)
+        L = 116.0 * (y / (3.0 * (6.0 / 29.0) ** 2) + 4.0 / 29.0) - 16.0
+        assert abs(lab[v, 0] - L) < 1e-9
+    # a* > 0 towards red, b* > 0 towards yellow, b* < 0 towards blue
+    red, yellow, blue = oracle.lab(np.array([0xFF0000, 0xFFFF00, 0x0000FF], dtype=np.uint32))
+    assert red[1] > 0 and yellow[2] > 0 and blue[2] < 0
+
+
+def test_lab_points_and_palette_round_trip():
+    # fixed point is round(value * 256); the inverse transform of an 8-bit colour's
+    # point rounds back to that colour (the quantisation error, 1/512 L*a*b* unit, is
+    # far below one 8-bit step); all 256 greys, the corners of the cube, 20000 colours
+    rng = np.random.default_rng(1976)
+    keys = np.concatenate([np.arange(256, dtype=np.uint32) * 0x010101,
+                           np.array([0, 0xFF0000, 0x00FF00, 0x0000FF, 0xFFFF00, 0xFF00FF, 0x00FFFF, 0xFFFFFF],
+                                    dtype=np.uint32),
+                           rng.integers(0, 1 << 24, size=20000).astype(np.uint32)])
+    pts = oracle.lab_points(keys)
+    lab = oracle.lab(keys[:300])
+    assert np.array_equal(pts[:300, :3], np.rint(lab * oracle.LAB_SCALE).astype(np.int32))
+    assert np.all(pts[:, 3] == 0)
+    pal = oracle.lab_palette(pts[:, :3].astype(np.float64))
+    assert np.array_equal(keys_of(pal), keys)
+    # out-of-gamut centres clamp: a very saturated L*a*b* point maps inside the cube
+    far = oracle.lab_palette(np.array([[60.0, 200.0, -200.0]]) * oracle.LAB_SCALE)
+    assert far.dtype == np.uint8 and far.shape == (1, 3)
+
+
+def test_points_lloyd_equals_rgb_lloyd_on_rgb_points(small_image):
+    # with each colour's three bytes as the point, the points path is exactly the
+    # RGB path: same labels, centres, SSE history and sums (pins assign/update/loop)
+    _, keys, w = small_image
+    pts = np.zeros((keys.size, 4), dtype=np.int32)
+    pts[:, :3] = rgb_of(keys)
+    for K, scheme in ((1, "FGY"), (7, "FGY"), (16, "KPP")):
+        seeds, _ = oracle.seed(keys, w, K, scheme, 31 + K)
+        a = oracle.lloyd(keys, w, seeds, 1e-4, 40)
+        b = oracle.lloyd_points(pts, w, seeds, 1e-4, 40)
+        assert a["iters"] == b["iters"] and np.array_equal(a["labels"], b["labels"])
+        assert np.array_equal(a["centers"], b["centers"]) and np.array_equal(a["sums"], b["sums"])
+        assert np.array_equal(a["sse_hist"], b["sse_hist"])
+    # Forgy among points draws the same indices as Forgy among colours
+    for K in (1, 5, 64):
+        want, _ = oracle.seed(keys, w, K, "FGY", 99)
+        assert np.array_equal(oracle.seed_points_fgy(pts, K, 99), want)
+
+
+def test_points_lloyd_invariants_in_lab(small_image):
+    # L*a*b* points: K = 1 gives the exact weighted mean, SSE never increases, every
+    # label is an argmin, centres are the exact weighted means of their labels, and
+    # the weighted run on unique colours equals the unweighted run on all pixels
+    img, keys, w = small_image
+    pts = oracle.lab_points(keys)
+    one = oracle.lloyd_points(pts, w, oracle.seed_points_fgy(pts, 1, 3), 1e-4, 10)
+    W = int(w.astype(np.int64).sum())
+    for ch in range(3):
+        S = int((w.astype(np.int64) * pts[:, ch].astype(np.int64)).sum())
+        assert one["centers"][0, ch] == S / W
+    seeds = oracle.seed_points_fgy(pts, 12, 8)
+    run = oracle.lloyd_points(pts, w, seeds, -1.0, 20)
+    h = run["sse_hist"]
+    assert np.all(h[1:] <= h[:-1] * (1 + 1e-12))
+    prev = oracle.lloyd_points(pts, w, seeds, -1.0, 19)["centers"]
+    d = ((pts[:, None, :3].astype(np.float64) - prev[None, :, :]) ** 2).sum(axis=2)
+    assert np.array_equal(run["labels"], np.argmin(d, axis=1))
+    for k in np.unique(run["labels"]):
+        m = run["labels"] == k
+        Wk = int(w[m].astype(np.int64).sum())
+        for ch in range(3):
+            Sk = int((w[m].astype(np.int64) * pts[m, ch].astype(np.int64)).sum())
+            assert run["centers"][k, ch] == Sk / Wk
+    px = img.reshape(-1, 3).astype(np.uint32)
+    pkeys = (px[:, 0] << 16) | (px[:, 1] << 8) | px[:, 2]
+    ppts = oracle.lab_points(pkeys)
+    full = oracle.lloyd_points(ppts, np.ones(pkeys.size, dtype=np.uint32), seeds, -1.0, 20)
+    assert np.allclose(full["centers"], run["centers"], rtol=0, atol=1e-9)
+    pos = np.searchsorted(keys, pkeys)
+    assert np.array_equal(full["labels"], run["labels"][pos])
