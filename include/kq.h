@@ -355,6 +355,51 @@ KQ_API int kq_set_wait_limit(void *ws, size_t ws_bytes, uint32_t wait_limit_us, 
  * *h_ndc (synchronizes `stream`). */
 KQ_API int kq_map_ndc_read(const void *ws, int64_t *h_ndc, kq_stream_t stream);
 
+/* ------------------------------------------------------------------ CIE L*a*b*
+ * k-means in the CIE L*a*b* colour space (Section 2.1 names L*a*b* beside RGB as a
+ * space k-means runs in): the unique colours of kq_histogram become L*a*b* points,
+ * Weighted Sort-Means runs on them (the same pruning, update and stop test as
+ * kq_lloyd), and each pixel takes the label of its colour.
+ *
+ * A point is one uint64_t: bits 0-15, 16-31 and 32-47 hold L*, a* and b* times 256,
+ * rounded to nearest (ties to even), as two's-complement 16-bit integers (every
+ * sRGB colour's L*a*b* lies within +-128); bits 48-63 are zero.  Centres are given
+ * in the same units (L*a*b* x 256) as FP64.
+ */
+
+/* L*a*b* point of each unique colour: 8-bit sRGB (IEC 61966-2-1) made linear, the
+ * sRGB matrix to CIE XYZ (D65), CIE 1976 L*a*b* relative to the D65 white
+ * (X_n = 0.95047, Y_n = 1, Z_n = 1.08883), all in FP64 with every operation
+ * rounded separately.  points: N' entries (device).  Asynchronous. */
+KQ_API int kq_lab_points(const uint32_t *keys, const int32_t *n_unique, uint64_t *points, kq_stream_t stream);
+
+/* Initial centres among the points (Section 2.3).  scheme: KQ_INIT_FGY only (K
+ * distinct points with the draws of kq_seed's Forgy; K >= N' gives the points in
+ * order, padded with the last).  centers: K x 3 FP64 in point units. */
+KQ_API int kq_seed_points(const uint64_t *points, const int32_t *n_unique, int32_t K, int32_t scheme, uint64_t seed,
+                          double *centers, kq_stream_t stream);
+
+/* Weighted Sort-Means on the points: kq_lloyd with the points' three coordinates in
+ * place of a colour's three bytes (exact int64 sums of weight x coordinate, FP64
+ * division, FP32 distances, the same pruning, ties and stop test).  No palette:
+ * kq_lab_palette turns the centres into sRGB colours. */
+KQ_API int kq_lloyd_points(const uint64_t *points, const uint32_t *weights, const int32_t *n_unique, int32_t K,
+                           double *centers, double eps, int32_t max_iter, uint32_t flags, uint8_t *labels,
+                           kq_lloyd_stats *stats, double *sse_hist, void *ws, size_t ws_bytes, kq_stream_t stream);
+
+/* sRGB palette of K centres in point units: the inverse of kq_lab_points (L*a*b* to
+ * XYZ to linear RGB by the inverse sRGB matrix, companding), each channel clamped
+ * to [0, 1] and rounded half up to 0..255, in FP64. */
+KQ_API int kq_lab_palette(const double *centers, int32_t K, uint8_t *palette, kq_stream_t stream);
+
+/* Mapping in L*a*b* (or any space Lloyd ran in over the unique colours): each
+ * pixel's index is the label of its colour in (keys, labels), as kq_histogram and
+ * kq_lloyd_points left them.  A pixel whose colour is not among `keys` gets 0 and
+ * sets KQ_EINVAL in the device status word.  Uses the workspace's colour table,
+ * which is zero again when the call's kernels finish. */
+KQ_API int kq_map_labels(const uint8_t *rgb, int64_t n_pixels, const uint32_t *keys, const int32_t *n_unique,
+                         const uint8_t *labels, uint8_t *idx, void *ws, size_t ws_bytes, kq_stream_t stream);
+
 /* Device status word of `ws` copied to *h_status (synchronizes `stream`). */
 KQ_API int kq_status_read(const void *ws, int32_t *h_status, kq_stream_t stream);
 

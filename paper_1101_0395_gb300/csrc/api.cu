@@ -157,6 +157,50 @@ int kq_map(const uint8_t *rgb, int64_t n_pixels, const uint8_t *palette, int32_t
     return kq::launch_map(rgb, n_pixels, palette, K, idx, sse_num, ws, L, (cudaStream_t)stream);
 }
 
+int kq_lab_points(const uint32_t *keys, const int32_t *n_unique, uint64_t *points, kq_stream_t stream)
+{
+    if (!keys || !n_unique || !points) return KQ_EINVAL;
+    return kq::launch_lab_points(keys, n_unique, reinterpret_cast<unsigned long long *>(points), (cudaStream_t)stream);
+}
+
+int kq_seed_points(const uint64_t *points, const int32_t *n_unique, int32_t K, int32_t scheme, uint64_t seed,
+                   double *centers, kq_stream_t stream)
+{
+    if (!points || !n_unique || !centers) return KQ_EINVAL;
+    if (K < 1 || K > kq::kMaxK || scheme != KQ_INIT_FGY) return KQ_EINVAL;
+    return kq::launch_seed_points(reinterpret_cast<const unsigned long long *>(points), n_unique, K, seed, centers,
+                                  (cudaStream_t)stream);
+}
+
+int kq_lloyd_points(const uint64_t *points, const uint32_t *weights, const int32_t *n_unique, int32_t K,
+                    double *centers, double eps, int32_t max_iter, uint32_t flags, uint8_t *labels,
+                    kq_lloyd_stats *stats, double *sse_hist, void *ws, size_t ws_bytes, kq_stream_t stream)
+{
+    Layout L;
+    if (!ws_ok(ws, ws_bytes, &L)) return KQ_EINVAL;
+    if (!points || !weights || !n_unique || !centers || !labels) return KQ_EINVAL;
+    if (K < 1 || K > kq::kMaxK || max_iter < 1 || eps != eps) return KQ_EINVAL;
+    if (flags & ~(KQ_LLOYD_LABELS_IN | KQ_LLOYD_DENSE)) return KQ_EINVAL;
+    return kq::launch_lloyd_points(reinterpret_cast<const unsigned long long *>(points), weights, n_unique, K, centers,
+                                   eps, max_iter, flags, labels, stats, sse_hist, ws, L, (cudaStream_t)stream);
+}
+
+int kq_lab_palette(const double *centers, int32_t K, uint8_t *palette, kq_stream_t stream)
+{
+    if (!centers || !palette || K < 1 || K > kq::kMaxK) return KQ_EINVAL;
+    return kq::launch_lab_palette(centers, K, palette, (cudaStream_t)stream);
+}
+
+int kq_map_labels(const uint8_t *rgb, int64_t n_pixels, const uint32_t *keys, const int32_t *n_unique,
+                  const uint8_t *labels, uint8_t *idx, void *ws, size_t ws_bytes, kq_stream_t stream)
+{
+    Layout L;
+    if (!ws_ok(ws, ws_bytes, &L)) return KQ_EINVAL;
+    if (n_pixels < 0 || !keys || !n_unique || !labels) return KQ_EINVAL;
+    if (n_pixels > 0 && (!rgb || !idx)) return KQ_EINVAL;
+    return kq::launch_map_labels(rgb, n_pixels, keys, n_unique, labels, idx, ws, L, (cudaStream_t)stream);
+}
+
 int kq_pixel_keys(const uint8_t *rgb, int64_t n_pixels, uint32_t *keys, uint32_t *weights, int32_t *n_out,
                   kq_stream_t stream)
 {

@@ -682,7 +682,7 @@ __device__ void group_lloyd(Group &g, const kq_batch_item &it, int64_t n, int K,
     a.sse_part = g.at_slot<float>(kSoSsep);
     a.rows = g.at_slot<uint32_t>(kSoRows);
     a.cent = g.at_slot<float4>(kSoCent);
-    lloyd_body(a, sh, row_cache, n, g.rank, g.C, g);
+    lloyd_body<RgbKeys>(a, sh, row_cache, n, g.rank, g.C, g);
     g();
 }
 

@@ -374,4 +374,13 @@ int launch_pixel_keys(const uint8_t *rgb, int64_t n, uint32_t *keys, uint32_t *w
                       cudaStream_t s);
 int launch_map(const uint8_t *rgb, int64_t n, const uint8_t *palette, int K, uint8_t *idx, int64_t *sse_num,
                void *ws, const Layout &L, cudaStream_t s);
+int launch_lloyd_points(const unsigned long long *pts, const uint32_t *w, const int32_t *n_unique, int K,
+                        double *centers, double eps, int max_iter, uint32_t flags, uint8_t *labels,
+                        kq_lloyd_stats *stats, double *sse_hist, void *ws, const Layout &L, cudaStream_t s);
+int launch_lab_points(const uint32_t *keys, const int32_t *n_unique, unsigned long long *pts, cudaStream_t s);
+int launch_seed_points(const unsigned long long *pts, const int32_t *n_unique, int K, uint64_t seed, double *centers,
+                       cudaStream_t s);
+int launch_lab_palette(const double *centers, int K, uint8_t *palette, cudaStream_t s);
+int launch_map_labels(const uint8_t *rgb, int64_t n, const uint32_t *keys, const int32_t *n_unique,
+                      const uint8_t *labels, uint8_t *idx, void *ws, const Layout &L, cudaStream_t s);
 }  // namespace kq

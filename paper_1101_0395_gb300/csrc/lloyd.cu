@@ -39,6 +39,7 @@ struct GridSync {
     __device__ __forceinline__ bool operator()() { return grid_sync(ctl, G, &epoch, limit_ns); }
 };
 
+template <class P>
 __global__ void __launch_bounds__(kLloydBlock, 1) lloyd_kernel(LloydArgs a)
 {
     __shared__ LloydShared sh;
@@ -49,19 +50,30 @@ __global__ void __launch_bounds__(kLloydBlock, 1) lloyd_kernel(LloydArgs a)
     const int G = (int)(want < 1 ? 1 : (want > gridDim.x ? gridDim.x : want));
     if ((int)blockIdx.x >= G) return;
     GridSync sync{a.ctl, (uint32_t)G + *(volatile const uint32_t *)&a.ctl->missing, 0u, wait_limit_ns(a.ctl)};
-    lloyd_body(a, sh, row_cache, n, (int)blockIdx.x, G, sync);
+    lloyd_body<P>(a, sh, row_cache, n, (int)blockIdx.x, G, sync);
 }
 
 // Dynamic shared memory: the row cache for the largest K (one size for every
 // launch, so the occupancy query and the cooperative grid are the same for all K).
 size_t lloyd_smem_bytes() { return sizeof(uint32_t) * (size_t)kMaxK * kRowStride + sizeof(float) * kChunkSlots; }
 
-int lloyd_smem_attr(size_t bytes)
+// One cooperative launch of the whole loop over points of kind P (the grid barrier's
+// arrival counter cleared on the stream first).
+template <class P>
+int launch_lloyd_kernel(LloydArgs &a, cudaStream_t s)
 {
-    return cudaFuncSetAttribute((const void *)lloyd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) ==
-                   cudaSuccess
-               ? KQ_OK
-               : KQ_ECUDA;
+    const void *fn = (const void *)lloyd_kernel<P>;
+    const size_t smem = lloyd_smem_bytes();
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return KQ_ECUDA;
+    const int per_sm = max_coresident(fn, kLloydBlock, smem);
+    if (per_sm < 1) return KQ_ECUDA;
+    int grid = device_info().sms * per_sm;
+    if (grid > kMaxGrid) grid = kMaxGrid;
+    if (cudaMemsetAsync(&a.ctl->bar_count, 0, sizeof(uint32_t), s) != cudaSuccess) return KQ_ECUDA;
+    void *args[] = {&a};
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kLloydBlock), args, smem, s) == cudaSuccess ? KQ_OK
+                                                                                                          : KQ_ECUDA;
 }
 
 }  // namespace
@@ -70,13 +82,6 @@ int launch_lloyd(const uint32_t *keys, const uint32_t *w, const int32_t *n_uniqu
                  int max_iter, uint32_t flags, uint8_t *labels, uint8_t *palette, kq_lloyd_stats *stats,
                  double *sse_hist, void *ws, const Layout &L, cudaStream_t s, int skip_if_n_le)
 {
-    const DeviceInfo di = device_info();
-    const size_t smem = lloyd_smem_bytes();
-    if (lloyd_smem_attr(smem) != KQ_OK) return KQ_ECUDA;
-    int per_sm = max_coresident((const void *)lloyd_kernel, kLloydBlock, smem);
-    if (per_sm < 1) return KQ_ECUDA;
-    int grid = di.sms * per_sm;
-    if (grid > kMaxGrid) grid = kMaxGrid;
     LloydArgs a;
     a.keys = keys;
     a.w = w;
@@ -98,11 +103,35 @@ int launch_lloyd(const uint32_t *keys, const uint32_t *w, const int32_t *n_uniqu
     a.sse_part = at<float>(ws, L.l_sse);
     a.rows = at<uint32_t>(ws, L.l_rows);
     a.cent = at<float4>(ws, L.l_cent);
-    // the grid barrier's arrival counter starts every launch at zero
-    if (cudaMemsetAsync(&a.ctl->bar_count, 0, sizeof(uint32_t), s) != cudaSuccess) return KQ_ECUDA;
-    void *args[] = {&a};
-    cudaError_t e = cudaLaunchCooperativeKernel((const void *)lloyd_kernel, dim3(grid), dim3(kLloydBlock), args, smem, s);
-    return e == cudaSuccess ? KQ_OK : KQ_ECUDA;
+    return launch_lloyd_kernel<RgbKeys>(a, s);
+}
+
+int launch_lloyd_points(const unsigned long long *pts, const uint32_t *w, const int32_t *n_unique, int K,
+                        double *centers, double eps, int max_iter, uint32_t flags, uint8_t *labels,
+                        kq_lloyd_stats *stats, double *sse_hist, void *ws, const Layout &L, cudaStream_t s)
+{
+    LloydArgs a;
+    a.keys = pts;
+    a.w = w;
+    a.n_unique = n_unique;
+    a.K = K;
+    a.eps = eps;
+    a.max_iter = max_iter;
+    a.flags = flags;
+    a.skip_if_n_le = 0;
+    a.centers = centers;
+    a.labels = labels;
+    a.palette = nullptr;
+    a.stats = stats;
+    a.sse_hist = sse_hist;
+    a.ctl = at<Ctl>(ws, L.ctl);
+    a.ndc = &a.ctl->ndc;
+    a.status = &a.ctl->status;
+    a.sums = at<unsigned long long>(ws, L.l_sums);
+    a.sse_part = at<float>(ws, L.l_sse);
+    a.rows = at<uint32_t>(ws, L.l_rows);
+    a.cent = at<float4>(ws, L.l_cent);
+    return launch_lloyd_kernel<FixedPoints>(a, s);
 }
 
 // ---------------------------------------------------------------- allocation-free variant
@@ -158,8 +187,10 @@ extern "C" KQ_API int kq_lloyd_noalloc(const uint32_t *keys, const uint32_t *wei
     if (cudaMemsetAsync(b + kNoAllocCtl, 0, sizeof(Ctl), s) != cudaSuccess) return KQ_ECUDA;
     const DeviceInfo di = device_info();
     const size_t smem = lloyd_smem_bytes();
-    if (lloyd_smem_attr(smem) != KQ_OK) return KQ_ECUDA;
-    int per_sm = max_coresident((const void *)lloyd_kernel, kLloydBlock, smem);
+    if (cudaFuncSetAttribute((const void *)lloyd_kernel<RgbKeys>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return KQ_ECUDA;
+    int per_sm = max_coresident((const void *)lloyd_kernel<RgbKeys>, kLloydBlock, smem);
     if (per_sm < 1) return KQ_ECUDA;
     int grid = di.sms * per_sm;
     if (grid > kMaxGrid) grid = kMaxGrid;
@@ -185,6 +216,7 @@ extern "C" KQ_API int kq_lloyd_noalloc(const uint32_t *keys, const uint32_t *wei
     a.rows = reinterpret_cast<uint32_t *>(b + kNoAllocRows);
     a.cent = reinterpret_cast<float4 *>(b + kNoAllocCent);
     void *args[] = {&a};
-    cudaError_t e = cudaLaunchCooperativeKernel((const void *)lloyd_kernel, dim3(grid), dim3(kLloydBlock), args, smem, s);
+    cudaError_t e =
+        cudaLaunchCooperativeKernel((const void *)lloyd_kernel<RgbKeys>, dim3(grid), dim3(kLloydBlock), args, smem, s);
     return e == cudaSuccess ? KQ_OK : KQ_ECUDA;
 }

@@ -25,8 +25,31 @@ constexpr int kDensePts = 2;   // points per lane in the full search
 constexpr float kPruneSlack = 1.0f + 0x1p-17f;
 constexpr unsigned kFull = 0xffffffffu;
 
+// The points the iteration runs on.  RgbKeys: unique colours as 24-bit keys, the
+// coordinates their bytes.  FixedPoints: fixed-point 3-D points (CIE L*a*b* x 256),
+// three signed 16-bit coordinates packed in a 64-bit word.  Either way the
+// coordinates are integers, so the weighted sums of a cluster are exact.
+struct RgbKeys {
+    using T = uint32_t;
+    static constexpr bool kRgb = true;
+    static constexpr unsigned long long kMaxAbs = 255;  // largest |coordinate|
+    __device__ __forceinline__ static T load(const void *p, int64_t i) { return static_cast<const T *>(p)[i]; }
+    __device__ __forceinline__ static int c0(T k) { return (int)key_r(k); }
+    __device__ __forceinline__ static int c1(T k) { return (int)key_g(k); }
+    __device__ __forceinline__ static int c2(T k) { return (int)key_b(k); }
+};
+struct FixedPoints {
+    using T = unsigned long long;
+    static constexpr bool kRgb = false;
+    static constexpr unsigned long long kMaxAbs = 32768;
+    __device__ __forceinline__ static T load(const void *p, int64_t i) { return static_cast<const T *>(p)[i]; }
+    __device__ __forceinline__ static int c0(T k) { return (int)(int16_t)(k & 0xFFFFull); }
+    __device__ __forceinline__ static int c1(T k) { return (int)(int16_t)((k >> 16) & 0xFFFFull); }
+    __device__ __forceinline__ static int c2(T k) { return (int)(int16_t)((k >> 32) & 0xFFFFull); }
+};
+
 struct LloydArgs {
-    const uint32_t *keys;
+    const void *keys;          // RgbKeys: uint32_t keys; FixedPoints: packed 64-bit points
     const uint32_t *w;
     const int32_t *n_unique;
     int K;
@@ -36,7 +59,7 @@ struct LloydArgs {
     int skip_if_n_le;
     double *centers;
     uint8_t *labels;
-    uint8_t *palette;
+    uint8_t *palette;          // RgbKeys only (K x 3 bytes); FixedPoints: unused
     kq_lloyd_stats *stats;
     double *sse_hist;
     Ctl *ctl;                  // grid barrier of the whole-grid launch (unused by groups)
@@ -335,18 +358,20 @@ __device__ __forceinline__ void dense_argmin_n(const LloydShared &sh, int K, con
     }
 }
 
-// Adds (w R, w G, w B, w) of each lane's point to its cluster's block sums.  When
-// all lanes of the warp chose the same cluster, one lane adds the warp total.
-// `narrow`: the block's whole slice has sum(w) * 255 < 2^32, so 32-bit sums are
-// exact and the native 32-bit shared-memory atomics can be used.
+// Adds (w x0, w x1, w x2, w) of each lane's point to its cluster's block sums
+// (two's-complement arithmetic, so signed coordinates add exactly).  When all lanes
+// of the warp chose the same cluster, one lane adds the warp total.  `narrow`: the
+// block's whole slice has sum(w) * max|x| < 2^31, so 32-bit sums are exact and the
+// native 32-bit shared-memory atomics can be used.
+template <class P>
 __device__ __forceinline__ void warp_accumulate(LloydShared &sh, bool narrow, bool active, int arg, uint32_t w,
-                                                uint32_t key)
+                                                typename P::T key)
 {
     const int a0 = __shfl_sync(kFull, arg, 0);
     const bool same = __all_sync(kFull, !active || arg == a0);
     if (narrow) {
         uint32_t W = active ? w : 0u;
-        uint32_t r = W * key_r(key), g = W * key_g(key), bb = W * key_b(key);
+        uint32_t r = W * (uint32_t)P::c0(key), g = W * (uint32_t)P::c1(key), bb = W * (uint32_t)P::c2(key);
         if (same) {
             for (int o = 16; o; o >>= 1) {
                 r += __shfl_down_sync(kFull, r, o);
@@ -369,7 +394,9 @@ __device__ __forceinline__ void warp_accumulate(LloydShared &sh, bool narrow, bo
         return;
     }
     unsigned long long W = active ? (unsigned long long)w : 0ull;
-    unsigned long long r = W * key_r(key), g = W * key_g(key), bb = W * key_b(key);
+    unsigned long long r = (unsigned long long)((long long)W * P::c0(key));
+    unsigned long long g = (unsigned long long)((long long)W * P::c1(key));
+    unsigned long long bb = (unsigned long long)((long long)W * P::c2(key));
     if (same) {
         for (int o = 16; o; o >>= 1) {
             r += __shfl_down_sync(kFull, r, o);
@@ -405,12 +432,13 @@ __device__ __forceinline__ float chunk_sse(float v)
 // count), one point of each per lane; labels, SSE and block sums.  The SSE goes to
 // the lane's running sum in chunk order, or (csse non-null) per chunk to csse[slot],
 // slot = (chunk - b) / G, the first chunk's slot being j0.
-template <int NP>
+template <class P, int NP>
 __device__ __forceinline__ void dense_step(const LloydArgs &a, LloydShared &sh, int K, int64_t n, int64_t c,
                                            int64_t S, int lane, bool narrow, float &sse32, unsigned long long &ndc,
                                            float *csse, int j0)
 {
-    uint32_t kk[NP], ww[NP];
+    typename P::T kk[NP];
+    uint32_t ww[NP];
     float px[NP], py[NP], pz[NP], bd[NP];
     int ga[NP];
 #pragma unroll
@@ -419,12 +447,12 @@ __device__ __forceinline__ void dense_step(const LloydArgs &a, LloydShared &sh, 
         kk[q] = 0u;
         ww[q] = 0u;
         if (iq < n) {
-            kk[q] = a.keys[iq];
+            kk[q] = P::load(a.keys, iq);
             ww[q] = a.w[iq];
         }
-        px[q] = (float)key_r(kk[q]);
-        py[q] = (float)key_g(kk[q]);
-        pz[q] = (float)key_b(kk[q]);
+        px[q] = (float)P::c0(kk[q]);
+        py[q] = (float)P::c1(kk[q]);
+        pz[q] = (float)P::c2(kk[q]);
     }
     dense_argmin_n<NP>(sh, K, px, py, pz, bd, ga);
 #pragma unroll
@@ -441,7 +469,7 @@ __device__ __forceinline__ void dense_step(const LloydArgs &a, LloydShared &sh, 
             const float t = chunk_sse(e);
             if (lane == 0) csse[j0 + q * kLloydBlock / 32] = t;
         }
-        warp_accumulate(sh, narrow, act, ga[q], ww[q], kk[q]);
+        warp_accumulate<P>(sh, narrow, act, ga[q], ww[q], kk[q]);
     }
 }
 
@@ -461,7 +489,7 @@ __device__ __forceinline__ void lloyd_failed_stats(const LloydArgs &a, int64_t n
     *a.stats = st;
 }
 
-template <class Sync>
+template <class P, class Sync>
 __device__ __forceinline__ void lloyd_body(const LloydArgs &a, LloydShared &sh, uint32_t *row_cache, int64_t n, int b,
                                            int G, Sync &sync)
 {
@@ -495,7 +523,7 @@ __device__ __forceinline__ void lloyd_body(const LloydArgs &a, LloydShared &sh, 
             if (i < n) sw += a.w[i];
         }
         sw = block_sum_u64<kLloydBlock>(sw, sh.red_u);
-        if (tid == 0) sh.narrow = sw * 255ull < (1ull << 32) ? 1 : 0;
+        if (tid == 0) sh.narrow = sw * P::kMaxAbs < (1ull << 31) ? 1 : 0;
         __syncthreads();
     }
     const bool narrow = sh.narrow != 0;
@@ -546,22 +574,23 @@ __device__ __forceinline__ void lloyd_body(const LloydArgs &a, LloydShared &sh, 
         const int64_t S = (int64_t)G * kWarps;
         int64_t c = b + (int64_t)G * warp;
         for (; !use_prev && c + (kDensePts - 1) * S < nch; c += kDensePts * S)
-            dense_step<kDensePts>(a, sh, K, n, c, S, lane, narrow, sse32, ndc, csse, (int)((c - b) / G));
+            dense_step<P, kDensePts>(a, sh, K, n, c, S, lane, narrow, sse32, ndc, csse, (int)((c - b) / G));
         for (; !use_prev && c < nch; c += S)
-            dense_step<1>(a, sh, K, n, c, S, lane, narrow, sse32, ndc, csse, (int)((c - b) / G));
+            dense_step<P, 1>(a, sh, K, n, c, S, lane, narrow, sse32, ndc, csse, (int)((c - b) / G));
         // The pruned loop does little arithmetic per colour, so the next chunk's key,
         // weight and previous label are loaded before the current chunk is scanned:
         // the memory latency overlaps the scan.
         // With csse (the balanced schedule, see kChunkSlots) the warps take the
         // block's chunks b + G j from a shared counter, so that a warp whose chunks
         // scan long rows does not hold up the block; the SSE is then kept per chunk.
-        uint32_t nkey = 0u, nw = 0u;
+        typename P::T nkey = 0;
+        uint32_t nw = 0u;
         int nlab = 0;
         int jc = warp;
         {
             const int64_t c0 = b + (int64_t)G * warp, i0 = c0 * 32 + lane;
             if (use_prev && c0 < nch && i0 < n) {
-                nkey = a.keys[i0];
+                nkey = P::load(a.keys, i0);
                 nw = a.w[i0];
                 nlab = a.labels[i0];
             }
@@ -569,7 +598,8 @@ __device__ __forceinline__ void lloyd_body(const LloydArgs &a, LloydShared &sh, 
         for (int64_t c = b + (int64_t)G * warp; use_prev && c < nch;) {
             const int64_t i = c * 32 + lane;
             const bool active = i < n;
-            uint32_t key = nkey, w = nw;
+            typename P::T key = nkey;
+            uint32_t w = nw;
             const int lab = nlab;
             int arg = 0;
             float best = 0.f;
@@ -582,7 +612,7 @@ __device__ __forceinline__ void lloyd_body(const LloydArgs &a, LloydShared &sh, 
             {
                 const int64_t i1 = cn * 32 + lane;
                 if (cn < nch && i1 < n) {
-                    nkey = a.keys[i1];
+                    nkey = P::load(a.keys, i1);
                     nw = a.w[i1];
                     nlab = a.labels[i1];
                 }
@@ -597,7 +627,7 @@ __device__ __forceinline__ void lloyd_body(const LloydArgs &a, LloydShared &sh, 
                 // of holding every lane of the warp.
                 int p = active ? lab : 0;
                 if (p >= K) p = 0;
-                const float x = (float)key_r(key), y = (float)key_g(key), z = (float)key_b(key);
+                const float x = (float)P::c0(key), y = (float)P::c1(key), z = (float)P::c2(key);
                 const float4 cp = sh.c[p];
                 const float prev = dist3(x, y, z, cp.x, cp.y, cp.z);
                 const float thr = __fmul_rn(4.0f * prev, kPruneSlack);
@@ -637,12 +667,12 @@ __device__ __forceinline__ void lloyd_body(const LloydArgs &a, LloydShared &sh, 
                 while (tail) {
                     const int q = __ffs(tail) - 1;
                     tail &= tail - 1;
-                    const uint32_t kq = __shfl_sync(kFull, key, q);
+                    const typename P::T kq = __shfl_sync(kFull, key, q);
                     const int pq = __shfl_sync(kFull, p, q);
                     const float thq = __shfl_sync(kFull, thr, q);
                     float qd = __shfl_sync(kFull, bd, q);
                     uint32_t qt = __shfl_sync(kFull, bt, q);
-                    const float qx = (float)key_r(kq), qy = (float)key_g(kq), qz = (float)key_b(kq);
+                    const float qx = (float)P::c0(kq), qy = (float)P::c1(kq), qz = (float)P::c2(kq);
                     const uint32_t *row = a.rows + (size_t)pq * Kp;
                     const uint32_t *rcq = row_cache + pq * kRowStride;
                     for (int j0 = jstop; j0 < Kp; j0 += 32) {
@@ -676,7 +706,7 @@ __device__ __forceinline__ void lloyd_body(const LloydArgs &a, LloydShared &sh, 
                     arg = (int)bt;
                 }
             } else if (active) {
-                dense_argmin(sh, K, (float)key_r(key), (float)key_g(key), (float)key_b(key), best, arg);
+                dense_argmin(sh, K, (float)P::c0(key), (float)P::c1(key), (float)P::c2(key), best, arg);
                 ndc += (unsigned long long)K;
             }
             const float e = active ? __fmul_rn((float)w, best) : 0.f;
@@ -689,7 +719,7 @@ __device__ __forceinline__ void lloyd_body(const LloydArgs &a, LloydShared &sh, 
                 const float t = chunk_sse(e);
                 if (lane == 0) csse[jc] = t;
             }
-            warp_accumulate(sh, narrow, active, arg, w, key);
+            warp_accumulate<P>(sh, narrow, active, arg, w, key);
             c = cn;
             jc = jn;
         }
@@ -703,7 +733,11 @@ __device__ __forceinline__ void lloyd_body(const LloydArgs &a, LloydShared &sh, 
         const unsigned long long bndc = block_sum_u64<kLloydBlock>(ndc, sh.red_u);
         __syncthreads();
         for (int j = tid; j < K * 4; j += kLloydBlock) {
-            const unsigned long long v = narrow ? (unsigned long long)sh.sum32[j] : sh.sum[j];
+            // 32-bit sums: coordinate sums of signed points are sign-extended, weights never
+            const unsigned long long v =
+                narrow ? ((!P::kRgb && (j & 3) != 3) ? (unsigned long long)(long long)(int32_t)sh.sum32[j]
+                                                     : (unsigned long long)sh.sum32[j])
+                       : sh.sum[j];
             if (v) atomicAdd(gsum + j, v);
         }
         if (tid == 0) {
@@ -737,7 +771,7 @@ __device__ __forceinline__ void lloyd_body(const LloydArgs &a, LloydShared &sh, 
             const int ch = warp - 1;
             for (int k = b + G * lane; k < K; k += G * 32) {
                 const unsigned long long W = __ldcg(gsum + 4 * k + 3);
-                if (W) sh.c64[3 * k + ch] = (double)__ldcg(gsum + 4 * k + ch) / (double)W;
+                if (W) sh.c64[3 * k + ch] = (double)(long long)__ldcg(gsum + 4 * k + ch) / (double)W;
             }
         }
         __syncthreads();
@@ -752,7 +786,7 @@ __device__ __forceinline__ void lloyd_body(const LloydArgs &a, LloydShared &sh, 
                 a.centers[3 * k] = x;
                 a.centers[3 * k + 1] = y;
                 a.centers[3 * k + 2] = z;
-                for (int ch = 0; ch < 3; ++ch) {
+                for (int ch = 0; P::kRgb && ch < 3; ++ch) {
                     int v;
                     if (W) {
                         const unsigned long long S = __ldcg(gsum + 4 * k + ch);

@@ -74,6 +74,12 @@ _SIGS = {
     "kq_status_clear": (C.c_int, [_vp, _vp]),
     "kq_set_wait_limit": (C.c_int, [_vp, C.c_size_t, C.c_uint32, C.c_uint32, _vp]),
     "kq_map_ndc_read": (C.c_int, [_vp, C.POINTER(C.c_int64), _vp]),
+    "kq_lab_points": (C.c_int, [_vp, _vp, _vp, _vp]),
+    "kq_seed_points": (C.c_int, [_vp, _vp, C.c_int32, C.c_int32, C.c_uint64, _vp, _vp]),
+    "kq_lloyd_points": (C.c_int, [_vp, _vp, _vp, C.c_int32, _vp, C.c_double, C.c_int32, C.c_uint32, _vp, _vp, _vp,
+                                  _vp, C.c_size_t, _vp]),
+    "kq_lab_palette": (C.c_int, [_vp, C.c_int32, _vp, _vp]),
+    "kq_map_labels": (C.c_int, [_vp, C.c_int64, _vp, _vp, _vp, _vp, _vp, C.c_size_t, _vp]),
     "kq_strerror": (C.c_char_p, [C.c_int]),
     "kq_batch_scratch_bytes": (C.c_size_t, [C.c_int32]),
     "kq_batch_workspace_size": (C.c_size_t, []),
@@ -189,6 +195,39 @@ def kq_status_read(ws: torch.Tensor, stream=None) -> int:
     return int(v.value)
 
 
+def kq_lab_points(keys: torch.Tensor, n_unique: torch.Tensor, points: torch.Tensor, stream=None) -> None:
+    _check("kq_lab_points", lib().kq_lab_points(_ptr(keys), _ptr(n_unique), _ptr(points), _stream(stream)))
+
+
+def kq_seed_points(points: torch.Tensor, n_unique: torch.Tensor, K: int, scheme, seed: int, centers: torch.Tensor,
+                   stream=None) -> None:
+    sch = INIT[scheme] if isinstance(scheme, str) else int(scheme)
+    _check("kq_seed_points", lib().kq_seed_points(_ptr(points), _ptr(n_unique), int(K), sch,
+                                                  int(seed) & ((1 << 64) - 1), _ptr(centers), _stream(stream)))
+
+
+def kq_lloyd_points(points: torch.Tensor, weights: torch.Tensor, n_unique: torch.Tensor, K: int,
+                    centers: torch.Tensor, eps: float, max_iter: int, labels: torch.Tensor, ws: torch.Tensor,
+                    stats: Optional[torch.Tensor] = None, sse_hist: Optional[torch.Tensor] = None, flags: int = 0,
+                    stream=None) -> None:
+    _check("kq_lloyd_points", lib().kq_lloyd_points(_ptr(points), _ptr(weights), _ptr(n_unique), int(K),
+                                                    _ptr(centers), float(eps), int(max_iter), int(flags),
+                                                    _ptr(labels), _ptr(stats), _ptr(sse_hist), _ptr(ws),
+                                                    ws.numel() * ws.element_size(), _stream(stream)))
+
+
+def kq_lab_palette(centers: torch.Tensor, K: int, palette: torch.Tensor, stream=None) -> None:
+    _check("kq_lab_palette", lib().kq_lab_palette(_ptr(centers), int(K), _ptr(palette), _stream(stream)))
+
+
+def kq_map_labels(rgb: torch.Tensor, keys: torch.Tensor, n_unique: torch.Tensor, labels: torch.Tensor,
+                  idx: torch.Tensor, ws: torch.Tensor, n_pixels: Optional[int] = None, stream=None) -> None:
+    n = rgb.numel() // 3 if n_pixels is None else int(n_pixels)
+    _check("kq_map_labels", lib().kq_map_labels(_ptr(rgb) if n else None, n, _ptr(keys), _ptr(n_unique),
+                                                _ptr(labels), _ptr(idx) if n else None, _ptr(ws),
+                                                ws.numel() * ws.element_size(), _stream(stream)))
+
+
 def kq_map_ndc_read(ws: torch.Tensor, stream=None) -> int:
     v = C.c_int64(0)
     _check("kq_map_ndc_read", lib().kq_map_ndc_read(_ptr(ws), C.byref(v), _stream(stream)))
@@ -285,6 +324,36 @@ class Quantizer:
                stream=stream)
         self.launches += (launches("kq_histogram", n) + launches("kq_seed", n, scheme, K) + launches("kq_lloyd")
                           + launches("kq_map", n))
+        return Result(idx=idx, palette=pal.view(K, 3), centers=c.view(K, 3), n_unique=self.n_unique,
+                      sse_num=self.sse_num, stats=self.stats)
+
+
+class LabQuantizer(Quantizer):
+    """k-means in the CIE L*a*b* colour space (Section 2.1): the unique colours'
+    L*a*b* points, Forgy seeds among them, Weighted Sort-Means on the points, the
+    centres' sRGB palette, and each pixel mapped to its colour's label.  Same
+    buffers as Quantizer plus the points; ``centers`` hold L*a*b* x 256 and
+    ``stats`` the Lloyd run in those units."""
+
+    def __init__(self, max_pixels: int, device=None):
+        super().__init__(max_pixels, device=device)
+        self.points = torch.zeros(self.capacity, dtype=torch.int64, device=self.device)
+
+    def quantize(self, rgb: torch.Tensor, K: int, scheme: str = "FGY", seed: int = 0, eps: float = 1e-4,
+                 max_iter: int = 100, flags: int = 0, stream=None) -> Result:
+        n = rgb.numel() // 3
+        if n > self.max_pixels:
+            raise ValueError("image larger than this LabQuantizer's max_pixels")
+        kq_histogram(rgb, self.keys, self.weights, self.n_unique, self.ws, stream=stream)
+        kq_lab_points(self.keys, self.n_unique, self.points, stream=stream)
+        c = self.centers[:3 * K]
+        kq_seed_points(self.points, self.n_unique, K, scheme, seed, c, stream=stream)
+        kq_lloyd_points(self.points, self.weights, self.n_unique, K, c, eps, max_iter, self.labels, self.ws,
+                        stats=self.stats, flags=flags, stream=stream)
+        pal = self.palette[:3 * K]
+        kq_lab_palette(c, K, pal, stream=stream)
+        idx = self.idx[:n]
+        kq_map_labels(rgb, self.keys, self.n_unique, self.labels, idx, self.ws, stream=stream)
         return Result(idx=idx, palette=pal.view(K, 3), centers=c.view(K, 3), n_unique=self.n_unique,
                       sse_num=self.sse_num, stats=self.stats)
 

@@ -17,7 +17,8 @@ def test_exports_every_declared_symbol():
                           "kq_lloyd_noalloc", "kq_status_read", "kq_status_clear", "kq_strerror",
                           "kq_batch_scratch_bytes", "kq_batch_workspace_size", "kq_batch_max_cluster",
                           "kq_batch_plan", "kq_batch_run", "kq_batch_tune", "kq_pixel_keys",
-                          "kq_histogram_strided", "kq_set_wait_limit", "kq_map_ndc_read"}
+                          "kq_histogram_strided", "kq_set_wait_limit", "kq_map_ndc_read",
+                          "kq_lab_points", "kq_seed_points", "kq_lloyd_points", "kq_lab_palette", "kq_map_labels"}
     L = kq.lib()
     for n in names:
         assert getattr(L, n) is not None
@@ -62,6 +63,16 @@ def test_invalid_arguments_are_rejected_synchronously():
     assert L.kq_status_read(None, None, None) == kq.KQ_EINVAL
     assert L.kq_set_wait_limit(None, size, 1000, 1, None) == kq.KQ_EINVAL
     assert L.kq_map_ndc_read(None, None, None) == kq.KQ_EINVAL
+    # the L*a*b* entry points
+    assert L.kq_lab_points(None, p, p, None) == kq.KQ_EINVAL
+    assert L.kq_seed_points(p, p, 8, 6, 1, p, None) == kq.KQ_EINVAL  # Forgy only
+    assert L.kq_seed_points(p, p, 0, 0, 1, p, None) == kq.KQ_EINVAL
+    assert L.kq_lloyd_points(p, p, p, 257, p, 1e-4, 10, 0, p, None, None, WS, size, None) == kq.KQ_EINVAL
+    assert L.kq_lloyd_points(p, p, p, 8, p, 1e-4, 0, 0, p, None, None, WS, size, None) == kq.KQ_EINVAL
+    assert L.kq_lloyd_points(p, p, p, 8, p, 1e-4, 10, 0, None, None, None, WS, size, None) == kq.KQ_EINVAL
+    assert L.kq_lab_palette(p, 0, p, None) == kq.KQ_EINVAL
+    assert L.kq_map_labels(p, 10, p, p, None, p, WS, size, None) == kq.KQ_EINVAL
+    assert L.kq_map_labels(p, 10, p, p, p, p, WS, 4096, None) == kq.KQ_EINVAL
     assert L.kq_set_wait_limit(WS, 4096, 1000, 1, None) == kq.KQ_EINVAL
     assert L.kq_workspace_init(None, size, None) == kq.KQ_EINVAL
 
