@@ -157,6 +157,36 @@ def measured_peaks() -> dict:
         return {}
 
 
+def profile_traffic(name: str):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the
+    committed ncu summary `profiles/<name>`, while the kernel's source still has the
+    SHA-256 recorded there; None once the source has changed or the summary is absent."""
+    import hashlib
+
+    try:
+        with open(os.path.join(ROOT, "profiles", name)) as f:
+            lines = f.read().splitlines()
+    except OSError:
+        return None, "profiles/%s absent" % name
+    sha = src = traffic = None
+    for ln in lines:
+        if ln.startswith("source_sha256:"):
+            parts = ln.split()
+            sha, src = parts[1], parts[2].strip("()")
+        elif ln.startswith("traffic_bytes_per_launch:"):
+            traffic = int(ln.split()[1])
+    if sha is None or traffic is None:
+        return None, "profiles/%s has no traffic line" % name
+    try:
+        with open(os.path.join(ROOT, src), "rb") as f:
+            now = hashlib.sha256(f.read()).hexdigest()
+    except OSError:
+        return None, "%s absent" % src
+    if now != sha:
+        return None, "%s changed since profiles/%s was captured" % (src, name)
+    return traffic, "profiles/%s (one ncu capture; %s unchanged since)" % (name, src)
+
+
 def cpu_baseline(img, K: int, eps: float, max_iter: int, budget_s: float = 12.0) -> dict:
     """The FP64 oracle, as it stands, on the host cores: whole quantizations of
     the same image until `budget_s` of CPU work (at least one)."""
@@ -998,9 +1028,10 @@ def run_gpu(args, rank, world, local) -> None:
     gdist_dense = n_unique * K * st["iters"] / lloyd_s / 1e9
     if dom == 2:
         achieved = st["ndc"] * FLOP_PER_DIST / lloyd_s / 1e12
+        traffic, tsrc = profile_traffic("lloyd_kernel_%s_k%d.txt" % (wl.name.replace("_", ""), K))
         roof = {"kernel": "lloyd_kernel (kq_lloyd: one persistent launch, all passes)", "bound": "alu",
                 "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                "traffic": None,
+                "traffic": traffic, "traffic_source": tsrc,
                 "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 FLOP x %.0f MHz (max SM clock, measured)"
                                % (props.multi_processor_count, sm_max),
                 "algorithmic": "%d FLOP per distance x NDC %d" % (FLOP_PER_DIST, st["ndc"])}
@@ -1014,9 +1045,10 @@ def run_gpu(args, rank, world, local) -> None:
         ops = 5.0 * n_unique * K
         achieved = ops / (stage_mean[1] * 1e-3) / 1e12
         cl = 16
+        traffic, tsrc = profile_traffic("seed_far_cluster_%s_k%d.txt" % (wl.name.replace("_", ""), K))
         roof = {"kernel": "seed_far_cluster (kq_seed, k-means++: one 16-CTA cluster, st.async/mbarrier exchanges)",
                 "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
-                "frac": achieved / alu_peak, "traffic": None,
+                "frac": achieved / alu_peak, "traffic": traffic, "traffic_source": tsrc,
                 "peak_source": "derived: %d SMs x 128 lanes x 1 op x %.0f MHz (max SM clock, measured)"
                                % (props.multi_processor_count, sm_max),
                 "algorithmic": "5 integer ops per unique colour per round x %d rounds" % K,
@@ -1024,8 +1056,7 @@ def run_gpu(args, rank, world, local) -> None:
                 "latency": {"us_per_round": 1e3 * stage_mean[1] / K, "rounds": K,
                             "exchanges_per_round": 2,
                             "note": "latency-bound: per round one push of every warp total to every CTA, one "
-                                    "push of the sampled key; the cluster's 16 SMs idle between them"},
-                "traffic_note": "DRAM traffic per launch: see profiles/seed_far_cluster_paper512_k256.txt"}
+                                    "push of the sampled key; the cluster's 16 SMs idle between them"}}
     else:
         byts = (3.0 * n + 8.0 * n_unique) if dom == 0 else (4.0 * n + 8.0 * n_unique)
         achieved = byts / (stage_mean[dom] * 1e-3) / 1e9

@@ -194,31 +194,43 @@ __device__ __forceinline__ uint32_t packed_d(const PixCtx &c, uint32_t x, uint32
     return xn + e.y - (__dp4a(x, e.x, 0u) << 9);
 }
 
+// The rarely taken part of the search, out of line so that the 16 inlined copies
+// of the common path stay small: inline slots FIX .. cnt - 1 (cnt <= 7), or, for a
+// cell with more candidates (cnt field 0xFF), its list in the workspace.
+__device__ __noinline__ uint32_t nearest_rest(const PixCtx &c, uint32_t x, uint32_t xn, unsigned long long d, int from,
+                                             uint32_t &nd)
+{
+    uint32_t best = 0xFFFFFFFFu;
+    const int cnt = (int)(d >> 56);
+    if (cnt <= kInline) {
+        for (int j = from; j < cnt; ++j) best = min(best, packed_d(c, x, xn, (uint32_t)(d >> (8 * j)) & 0xFFu));
+        nd += (uint32_t)(cnt - from);
+    } else {
+        const int m = (int)(d & 0x1FFu);
+        const uint8_t *l = c.list + (size_t)map_cell(x) * kMaxK;
+        for (int j = 0; j < m; ++j) best = min(best, packed_d(c, x, xn, __ldg(l + j)));
+        nd += (uint32_t)m;
+    }
+    return best;
+}
+
 // Nearest palette entry of colour x, packed as (d << 8) | k, from its cell's
 // descriptor d; `nd` counts the distances computed.  The first FIX slots are
 // evaluated without a branch (a cell has at least one candidate, and unused slots
-// repeat the first); only cells with more candidates loop.  FIX grows with K,
-// since larger palettes give cells more candidates.
+// repeat the first); cells with more candidates finish in nearest_rest.  FIX grows
+// with K, since larger palettes give cells more candidates.
 template <int FIX>
 __device__ __forceinline__ uint32_t nearest(const PixCtx &c, uint32_t x, unsigned long long d, uint32_t &nd)
 {
     const uint32_t xn = __dp4a(x, x, 0u) << 8;
     const int cnt = (int)(d >> 56);
-    uint32_t best;
-    if (cnt <= kInline) {
-        const uint32_t lo = (uint32_t)d;
-        best = packed_d(c, x, xn, lo & 0xFFu);
-        if (FIX > 1) best = min(best, packed_d(c, x, xn, (lo >> 8) & 0xFFu));
-        if (FIX > 2) best = min(best, packed_d(c, x, xn, (lo >> 16) & 0xFFu));
-        for (int j = FIX; j < cnt; ++j) best = min(best, packed_d(c, x, xn, (uint32_t)(d >> (8 * j)) & 0xFFu));
-        nd += (uint32_t)cnt;
-    } else {
-        const int m = (int)(d & 0x1FFu);
-        const uint8_t *l = c.list + (size_t)map_cell(x) * kMaxK;
-        best = 0xFFFFFFFFu;
-        for (int j = 0; j < m; ++j) best = min(best, packed_d(c, x, xn, __ldg(l + j)));
-        nd += (uint32_t)m;
-    }
+    if (cnt > kInline) return nearest_rest(c, x, xn, d, 0, nd);
+    const uint32_t lo = (uint32_t)d;
+    uint32_t best = packed_d(c, x, xn, lo & 0xFFu);
+    if (FIX > 1) best = min(best, packed_d(c, x, xn, (lo >> 8) & 0xFFu));
+    if (FIX > 2) best = min(best, packed_d(c, x, xn, (lo >> 16) & 0xFFu));
+    nd += (uint32_t)(cnt < FIX ? cnt : FIX);
+    if (cnt > FIX) best = min(best, nearest_rest(c, x, xn, d, FIX, nd));
     return best;
 }
 

@@ -134,3 +134,31 @@ def test_strided_histogram_matches_oracle_on_the_subsample(h, w, stride, pad):
     assert n == keys_o.size
     assert np.array_equal(u32(keys[:n]), keys_o) and np.array_equal(u32(wts[:n]), w_o)
     assert int(u32(wts[:n]).sum()) == ((h + stride - 1) // stride) * ((w + stride - 1) // stride)
+
+
+
+@pytest.mark.parametrize("offset", [0, 7])
+def test_large_misaligned_and_capacity(offset):
+    # a misaligned 2^22 + 13 pixel image (head and tail pixels outside the 16-pixel
+    # groups) with many singleton colours, twice on one workspace, then with room
+    # for only a third of its colours
+    rng = np.random.default_rng(4242 + offset)
+    n = (1 << 22) + 13
+    base = synth.WORKLOADS["paper_512"].make(5).reshape(-1, 3)
+    img = base[rng.integers(0, base.shape[0], size=n)]
+    img[: n // 5] = rng.integers(0, 256, size=(n // 5, 3), dtype=np.uint8)
+    ok, ow = oracle.histogram(img)
+    buf = torch.zeros(3 * n + 64, dtype=torch.uint8, device="cuda")
+    buf[offset:offset + 3 * n] = to_dev(img.reshape(-1))
+    r = Run(img)
+    r.rgb = buf[offset:offset + 3 * n]
+    keys, w = r.histogram()
+    assert np.array_equal(keys, ok) and np.array_equal(w, ow)
+    assert r.status() == kq.KQ_OK
+    keys2, w2 = r.histogram()
+    assert np.array_equal(keys2, ok) and np.array_equal(w2, ow)
+    cap = ok.size // 3
+    rc = Run(img, capacity=cap)
+    kc, wc = rc.histogram()
+    assert kc.size == cap and np.array_equal(kc, ok[:cap]) and np.array_equal(wc, ow[:cap])
+    assert rc.status() == kq.KQ_ECAPACITY
