@@ -300,9 +300,9 @@ KQ_API int kq_batch_tune(const kq_batch_item *h_items, const kq_batch_item *item
  * must not trigger the device-wide synchronisation of cudaMalloc/cudaFree).
  *
  * Same arguments, results and device-side behaviour as kq_lloyd, minus `ws`.
- * Its scratch (control block, cluster sums, SSE partials, the sorted
- * centre-distance rows and the FP32 centres) is one static device array of
- * 360,448 bytes inside libkq.so; every GPU that loads the library holds it
+ * Its scratch (control block, cluster sums, SSE partials and the sorted
+ * centre-distance rows) is one static device array of 356,352 bytes inside
+ * libkq.so; every GPU that loads the library holds it
  * until the process exits.
  *  - Limit: K <= 256 (the array holds sums and rows for 256 centres); K > 256,
  *    like any invalid argument, returns KQ_EINVAL.

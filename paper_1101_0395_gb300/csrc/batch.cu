@@ -61,8 +61,7 @@ constexpr size_t kSoWl = kSoSumm + sizeof(uint32_t) * (size_t)kSummWords;
 constexpr size_t kSoSums = kSoWl + sizeof(uint32_t) * (size_t)kBitWords;
 constexpr size_t kSoSsep = kSoSums + sizeof(unsigned long long) * 3 * kMaxK * 4;
 constexpr size_t kSoRows = kSoSsep + sizeof(float) * 2 * kMaxGrid;
-constexpr size_t kSoCent = kSoRows + sizeof(uint32_t) * kMaxK * kMaxK;
-constexpr size_t kSoChunk = kSoCent + sizeof(float4) * kMaxK;
+constexpr size_t kSoChunk = kSoRows + sizeof(uint32_t) * kMaxK * kMaxK;
 constexpr size_t kSoWu = kSoChunk + sizeof(uint32_t) * kBatchChunks * 3 * 256;
 constexpr size_t kSoMisc = kSoWu + kWuBytes;
 constexpr size_t kSlotBytes = (kSoMisc + sizeof(SlotMisc) + 4095) / 4096 * 4096;
@@ -681,7 +680,6 @@ __device__ void group_lloyd(Group &g, const kq_batch_item &it, int64_t n, int K,
     a.sums = g.at_slot<unsigned long long>(kSoSums);
     a.sse_part = g.at_slot<float>(kSoSsep);
     a.rows = g.at_slot<uint32_t>(kSoRows);
-    a.cent = g.at_slot<float4>(kSoCent);
     lloyd_body<RgbKeys>(a, sh, row_cache, n, g.rank, g.C, g);
     g();
 }

@@ -57,7 +57,7 @@ static_assert(offsetof(Ctl, bar_count) == 128, "the barrier counter has its own 
 // ---------------------------------------------------------------- workspace layout
 struct Layout {
     size_t ctl, hist_cnt, hist_bits, hist_chunk, m_desc, m_list;
-    size_t l_sums, l_sse, l_rows, l_cent;
+    size_t l_sums, l_sse, l_rows;
     size_t s_d2, s_part, s_slot, s_chunk, s_gcnt, s_misc, s_labels, s_centers, s_wu, s_gpart;
     size_t total;
     int64_t max_unique;
@@ -89,7 +89,6 @@ __host__ __device__ inline Layout layout_for(int64_t max_unique)
     L.l_sums = take(sizeof(unsigned long long) * 3 * kMaxK * 4);
     L.l_sse = take(sizeof(double) * 2 * kMaxGrid);
     L.l_rows = take(sizeof(uint32_t) * kMaxK * kMaxK);
-    L.l_cent = take(sizeof(float4) * kMaxK);
     L.s_part = take(sizeof(unsigned long long) * 2 * kMaxGrid);
     L.s_slot = take(sizeof(unsigned long long) * kMaxK);
     L.s_chunk = take(sizeof(uint32_t) * (size_t)kSeedChunks * 3 * 256);

@@ -16,15 +16,17 @@
 //      pass balances its chunks over the warps), so the sum is deterministic; the
 //      blocks' partials are added in block order, also in FP32.
 //   -- grid barrier --
-//   B. update: every block evaluates SSE_i (a fixed-order sum of the block
-//      partials) and the stopping test of Section 3.3 identically; block b divides
-//      the sums of the clusters it owns (k = b, b + G, ...) in FP64 (an empty
-//      cluster keeps its centre) and publishes their FP32 copies.
-//   -- grid barrier --
-//   C. every block loads all FP32 centres; with pruning it builds its rows of the
-//      squared centre-to-centre distance table, each sorted ascending and packed as
-//      (distance bits with the low 8 cleared) | index.
+//   B. update, in every block: SSE_i (a fixed-order sum of the block partials)
+//      and the stopping test of Section 3.3, evaluated identically; every
+//      cluster's FP32 centre, the FP32 number nearest to the exact quotient S / W
+//      of its integer sums (an empty cluster keeps its centre), so that no block
+//      waits for another's; block b also divides the sums of the clusters it owns
+//      (k = b, b + G, ...) in FP64, the centres returned when the loop stops.
+//   C. with pruning, block b builds its rows of the squared centre-to-centre
+//      distance table, each sorted ascending and packed as (distance bits with the
+//      low 8 cleared) | index.
 //   -- grid barrier (pruning only) --
+// A pass therefore has two grid barriers with pruning, one without.
 #include "lloyd_body.cuh"
 
 namespace kq {
@@ -102,7 +104,6 @@ int launch_lloyd(const uint32_t *keys, const uint32_t *w, const int32_t *n_uniqu
     a.sums = at<unsigned long long>(ws, L.l_sums);
     a.sse_part = at<float>(ws, L.l_sse);
     a.rows = at<uint32_t>(ws, L.l_rows);
-    a.cent = at<float4>(ws, L.l_cent);
     return launch_lloyd_kernel<RgbKeys>(a, s);
 }
 
@@ -130,22 +131,20 @@ int launch_lloyd_points(const unsigned long long *pts, const uint32_t *w, const 
     a.sums = at<unsigned long long>(ws, L.l_sums);
     a.sse_part = at<float>(ws, L.l_sse);
     a.rows = at<uint32_t>(ws, L.l_rows);
-    a.cent = at<float4>(ws, L.l_cent);
     return launch_lloyd_kernel<FixedPoints>(a, s);
 }
 
 // ---------------------------------------------------------------- allocation-free variant
 // kq_lloyd_noalloc runs the same kernel as kq_lloyd, with its scratch (control
-// block, cluster sums, SSE partials, centre-distance rows, published centres) in
-// one file-scope device array instead of a caller-allocated workspace.
+// block, cluster sums, SSE partials, centre-distance rows) in one file-scope
+// device array instead of a caller-allocated workspace.
 namespace {
 
 constexpr size_t kNoAllocCtl = 0;
 constexpr size_t kNoAllocSums = 4096;
 constexpr size_t kNoAllocSse = kNoAllocSums + sizeof(unsigned long long) * 3 * kMaxK * 4;
 constexpr size_t kNoAllocRows = kNoAllocSse + sizeof(double) * 2 * kMaxGrid;
-constexpr size_t kNoAllocCent = kNoAllocRows + sizeof(uint32_t) * kMaxK * kMaxK;
-constexpr size_t kNoAllocBytes = kNoAllocCent + sizeof(float4) * kMaxK;  // 360,448 bytes
+constexpr size_t kNoAllocBytes = kNoAllocRows + sizeof(uint32_t) * kMaxK * kMaxK;  // 356,352 bytes
 static_assert(sizeof(Ctl) <= kNoAllocSums, "control block fits its slot");
 
 // Shared by every call on a device and kept for the life of the process.
@@ -214,7 +213,6 @@ extern "C" KQ_API int kq_lloyd_noalloc(const uint32_t *keys, const uint32_t *wei
     a.sums = reinterpret_cast<unsigned long long *>(b + kNoAllocSums);
     a.sse_part = reinterpret_cast<float *>(b + kNoAllocSse);
     a.rows = reinterpret_cast<uint32_t *>(b + kNoAllocRows);
-    a.cent = reinterpret_cast<float4 *>(b + kNoAllocCent);
     void *args[] = {&a};
     cudaError_t e =
         cudaLaunchCooperativeKernel((const void *)lloyd_kernel<RgbKeys>, dim3(grid), dim3(kLloydBlock), args, smem, s);

@@ -68,7 +68,6 @@ struct LloydArgs {
     unsigned long long *sums;  // [3][kMaxK][4]: pass i adds into buffer i % 3
     float *sse_part;           // [2][kMaxGrid] block SSE partials (FP32, fixed-order trees)
     uint32_t *rows;            // [K][Kp], Kp = K rounded up to a multiple of 4
-    float4 *cent;              // [K] FP32 centres published by their owner blocks
 };
 
 struct LloydShared {
@@ -206,12 +205,57 @@ __device__ __forceinline__ void build_rows(LloydShared &sh, int K, int b, int G,
     else build_rows_t<8>(sh, K, b, G, rows);
 }
 
+// The FP32 number nearest to the exact quotient num / W (ties to even), W > 0: a
+// cluster's FP32 centre coordinate from its exact integer sums.  The FP32 first
+// guess f = m 2^e (three roundings) is within two units in the last place; each
+// step checks it exactly with the 128-bit residual D = s 2^(1-e) - 2 m W, i.e.
+// 2 (s / W - f) in units of W 2^(e-1): f is the nearest when |D| < W (half a unit
+// in the last place; a quarter below a power of two) and moves one unit toward
+// s / W otherwise, a tie going to the even neighbour.  (For W < 2^28 the result is
+// also (float)((double)num / (double)W): a quotient whose denominator is below
+// 2^28 cannot fall within 2^-53 of a midpoint without being on it.)
+__device__ __forceinline__ float div_rn_exact(long long num, unsigned long long W)
+{
+    if (num == 0) return 0.f;
+    const bool neg = num < 0;
+    const unsigned long long s = neg ? 0ull - (unsigned long long)num : (unsigned long long)num;
+    uint32_t u = __float_as_uint(__fdiv_rn(__ull2float_rn(s), __ull2float_rn(W)));
+    for (int step = 0; step < 4; ++step) {
+        const unsigned long long m = (unsigned long long)((u & 0x7FFFFFu) | 0x800000u);
+        const int sh = 1 - ((int)(u >> 23) - 150);  // 1 - e
+        unsigned __int128 A = s, B = (unsigned __int128)(2ull * m) * W, T = W;
+        if (sh >= 0) A <<= sh;
+        else {
+            B <<= -sh;
+            T <<= -sh;
+        }
+        if (A >= B) {
+            const unsigned __int128 D = A - B;
+            if (D < T || (D == T && !(m & 1ull))) break;
+            ++u;
+        } else {
+            // below a power of two the next FP32 number down is half as far
+            const unsigned __int128 D = m == 0x800000ull ? (B - A) << 1 : B - A;
+            if (D < T || (D == T && !(m & 1ull))) break;
+            --u;
+        }
+    }
+    return neg ? -__uint_as_float(u) : __uint_as_float(u);
+}
+
 __device__ __forceinline__ void set_centre(LloydShared &sh, int k, float4 c)
 {
     sh.c[k] = c;
     sh.cx[k] = c.x;
     sh.cy[k] = c.y;
     sh.cz[k] = c.z;
+}
+
+// Channel ch of centre k (the float4 and the per-channel copies).
+__device__ __forceinline__ void set_coord(LloydShared &sh, int k, int ch, float v)
+{
+    reinterpret_cast<float *>(&sh.c[k])[ch] = v;
+    (ch == 0 ? sh.cx : ch == 1 ? sh.cy : sh.cz)[k] = v;
 }
 
 // Full search over all K centres with the lowest index winning ties.  Distances are
@@ -749,9 +793,11 @@ __device__ __forceinline__ void lloyd_body(const LloydArgs &a, LloydShared &sh, 
             return;
         }
 
-        // ---- B: SSE, stopping test, owned centres.  FP64 instructions are slow on
-        // this GPU, so the stopping test (warp 0) and the three channel divisions of
-        // the owned clusters (warps 1-3) run in different warps.
+        // ---- B: every block derives every cluster's FP32 centre itself from the exact
+        // sums (the FP32 number nearest to S / W), so no block waits for another
+        // before its rows or its next assignment.  Warp 0 evaluates SSE_i and the
+        // stopping test; warps 1-3 divide the sums of the clusters the block owns
+        // (k = b, b + G, ...) in FP64, the centres returned when the loop stops.
         ++it;
         if (warp == 0) {
             float s = 0.f;
@@ -773,16 +819,23 @@ __device__ __forceinline__ void lloyd_body(const LloydArgs &a, LloydShared &sh, 
                 const unsigned long long W = __ldcg(gsum + 4 * k + 3);
                 if (W) sh.c64[3 * k + ch] = (double)(long long)__ldcg(gsum + 4 * k + ch) / (double)W;
             }
+        } else {
+            // one (cluster, channel) per thread and step; an empty cluster keeps its
+            // centre (its FP32 copy is left as it is)
+            for (int j = tid - 128; j < 3 * K; j += kLloydBlock - 128) {
+                const int k = j / 3, ch = j - 3 * k;
+                const unsigned long long W = __ldcg(gsum + 4 * k + 3);
+                if (W) set_coord(sh, k, ch, div_rn_exact((long long)__ldcg(gsum + 4 * k + ch), W));
+            }
         }
         __syncthreads();
         const double sse_i = sh.sse_i;
         const bool conv = sh.conv != 0;
         const bool stop = conv || it >= a.max_iter;
-        for (int k = b + G * tid; k < K; k += G * kLloydBlock) {
-            const unsigned long long W = __ldcg(gsum + 4 * k + 3);
-            const double x = sh.c64[3 * k], y = sh.c64[3 * k + 1], z = sh.c64[3 * k + 2];
-            a.cent[k] = make_float4((float)x, (float)y, (float)z, 0.f);
-            if (stop) {
+        if (stop) {
+            for (int k = b + G * tid; k < K; k += G * kLloydBlock) {
+                const unsigned long long W = __ldcg(gsum + 4 * k + 3);
+                const double x = sh.c64[3 * k], y = sh.c64[3 * k + 1], z = sh.c64[3 * k + 2];
                 a.centers[3 * k] = x;
                 a.centers[3 * k + 1] = y;
                 a.centers[3 * k + 2] = z;
@@ -819,14 +872,9 @@ __device__ __forceinline__ void lloyd_body(const LloydArgs &a, LloydShared &sh, 
         }
         if (stop) return;
         prev_sse = sse_i;
-        if (!sync()) {
-            if (b == 0) lloyd_failed_stats(a, n, it);
-            return;
-        }
 
-        // ---- C: all centres, then this block's rows of the distance table
-        for (int k = tid; k < K; k += kLloydBlock) set_centre(sh, k, __ldcg(a.cent + k));
-        __syncthreads();
+        // ---- C: this block's rows of the distance table (pruning only), from the
+        // centres every block now holds
         if (prune) {
             build_rows(sh, K, b, G, a.rows);
             if (!sync()) {
