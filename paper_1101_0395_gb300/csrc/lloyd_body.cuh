@@ -624,9 +624,6 @@ __device__ __forceinline__ void lloyd_body(const LloydArgs &a, LloydShared &sh, 
         // The pruned loop does little arithmetic per colour, so the next chunk's key,
         // weight and previous label are loaded before the current chunk is scanned:
         // the memory latency overlaps the scan.
-        // With csse (the balanced schedule, see kChunkSlots) the warps take the
-        // block's chunks b + G j from a shared counter, so that a warp whose chunks
-        // scan long rows does not hold up the block; the SSE is then kept per chunk.
         typename P::T nkey = 0;
         uint32_t nw = 0u;
         int nlab = 0;
@@ -639,6 +636,9 @@ __device__ __forceinline__ void lloyd_body(const LloydArgs &a, LloydShared &sh, 
                 nlab = a.labels[i0];
             }
         }
+        // With csse (the balanced schedule, see kChunkSlots) the warps take the
+        // block's chunks b + G j from a shared counter, so that a warp whose chunks
+        // scan long rows does not hold up the block; the SSE is then kept per chunk.
         for (int64_t c = b + (int64_t)G * warp; use_prev && c < nch;) {
             const int64_t i = c * 32 + lane;
             const bool active = i < n;
@@ -681,16 +681,25 @@ __device__ __forceinline__ void lloyd_body(const LloydArgs &a, LloydShared &sh, 
                 const uint32_t *rc = row_cache + p * kRowStride;
                 const int jl = Kp < kRowCache ? Kp : kRowCache;
                 int jstop = jl;
-                for (int j = 0; j < jl; ++j) {
+                // Four row entries per step: their loads are independent, and since a
+                // row ascends, an entry is within the bound exactly when every entry
+                // before it is; only those entries' centres are loaded and their
+                // distances evaluated (in row order, so the running minimum is the
+                // one-at-a-time scan's).
+                for (int j = 0; j < jl; j += 4) {
                     if (!done) {
-                        const uint32_t e = rc[j];
-                        if (__uint_as_float(e & 0xFFFFFF00u) > thr) {
-                            done = true;
-                        } else {
-                            const uint32_t t = e & 0xFFu;
-                            if (t != (uint32_t)p) {
-                                const float4 ct = sh.c[t];
-                                const float d = dist3(x, y, z, ct.x, ct.y, ct.z);
+                        uint32_t e[4];
+                        float4 ct[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) e[q] = rc[j + q];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) ct[q] = sh.c[e[q] & 0xFFu];  // every index is < K
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const bool in = !(__uint_as_float(e[q] & 0xFFFFFF00u) > thr);
+                            const uint32_t t = e[q] & 0xFFu;
+                            if (in && t != (uint32_t)p) {
+                                const float d = dist3(x, y, z, ct[q].x, ct[q].y, ct[q].z);
                                 ++ndc;
                                 if (d < bd || (d == bd && t < bt)) {
                                     bd = d;
@@ -698,13 +707,12 @@ __device__ __forceinline__ void lloyd_body(const LloydArgs &a, LloydShared &sh, 
                                 }
                             }
                         }
+                        done = __uint_as_float(e[3] & 0xFFFFFF00u) > thr;
                     }
-                    if ((j & 3) == 3) {
-                        const unsigned left = __ballot_sync(kFull, !done);
-                        if (__popc(left) <= kCoopLanes) {
-                            jstop = j + 1;
-                            break;
-                        }
+                    const unsigned left = __ballot_sync(kFull, !done);
+                    if (__popc(left) <= kCoopLanes) {
+                        jstop = j + 4;
+                        break;
                     }
                 }
                 unsigned tail = __ballot_sync(kFull, !done && Kp > jstop);
@@ -773,9 +781,24 @@ __device__ __forceinline__ void lloyd_body(const LloydArgs &a, LloydShared &sh, 
             sse32 = 0.f;
             for (int jj = tid; jj < nslot; jj += kLloydBlock) sse32 = __fadd_rn(sse32, csse[jj]);
         }
-        const float bsse = block_sum_f32<kLloydBlock>(sse32, sh.red_f);
-        const unsigned long long bndc = block_sum_u64<kLloydBlock>(ndc, sh.red_u);
+        // the block's SSE (a fixed shuffle tree per warp, then the warps in order)
+        // and distance count, valid in thread 0
+        float bsse = 0.f;
+        unsigned long long bndc = 0ull;
+        for (int o = 16; o; o >>= 1) {
+            sse32 = __fadd_rn(sse32, __shfl_down_sync(kFull, sse32, o));
+            ndc += __shfl_down_sync(kFull, ndc, o);
+        }
+        if (lane == 0) {
+            sh.red_f[warp] = sse32;
+            sh.red_u[warp] = ndc;
+        }
         __syncthreads();
+        if (tid == 0)
+            for (int i = 0; i < kWarps; ++i) {
+                bsse = __fadd_rn(bsse, sh.red_f[i]);
+                bndc += sh.red_u[i];
+            }
         for (int j = tid; j < K * 4; j += kLloydBlock) {
             // 32-bit sums: coordinate sums of signed points are sign-extended, weights never
             const unsigned long long v =
@@ -852,11 +875,14 @@ __device__ __forceinline__ void lloyd_body(const LloydArgs &a, LloydShared &sh, 
                 }
             }
         }
-        if (b == 0) {
+        {
             // Buffer (pass + 1) % 3 was last read in the previous pass and is next added
-            // into two passes from now, after barriers this block must reach first.
+            // into two passes from now, after barriers every block must reach first;
+            // the blocks clear it in slices, so that no block lags behind the others.
             unsigned long long *ahead = a.sums + (size_t)((it + 1) % 3) * kMaxK * 4;
-            for (int j = tid; j < kMaxK * 4; j += kLloydBlock) ahead[j] = 0ull;
+            for (int j = b + G * tid; j < K * 4; j += G * kLloydBlock) ahead[j] = 0ull;
+        }
+        if (b == 0) {
             if (tid == 0 && a.sse_hist) a.sse_hist[it - 1] = sse_i;
             if (stop && tid == 0 && a.stats) {
                 kq_lloyd_stats st;
