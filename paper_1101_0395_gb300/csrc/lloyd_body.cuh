@@ -686,16 +686,16 @@ __device__ __forceinline__ void lloyd_body(const LloydArgs &a, LloydShared &sh, 
                 // before it is; only those entries' centres are loaded and their
                 // distances evaluated (in row order, so the running minimum is the
                 // one-at-a-time scan's).
-                for (int j = 0; j < jl; j += 4) {
+                for (int j = 0; j < jl; j += 8) {
                     if (!done) {
-                        uint32_t e[4];
-                        float4 ct[4];
+                        uint32_t e[8];
+                        float4 ct[8];
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) e[q] = rc[j + q];
+                        for (int q = 0; q < 8; ++q) e[q] = rc[j + q];
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) ct[q] = sh.c[e[q] & 0xFFu];  // every index is < K
+                        for (int q = 0; q < 8; ++q) ct[q] = sh.c[e[q] & 0xFFu];  // every index is < K
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
+                        for (int q = 0; q < 8; ++q) {
                             const bool in = !(__uint_as_float(e[q] & 0xFFFFFF00u) > thr);
                             const uint32_t t = e[q] & 0xFFu;
                             if (in && t != (uint32_t)p) {
@@ -707,11 +707,11 @@ __device__ __forceinline__ void lloyd_body(const LloydArgs &a, LloydShared &sh, 
                                 }
                             }
                         }
-                        done = __uint_as_float(e[3] & 0xFFFFFF00u) > thr;
+                        done = __uint_as_float(e[7] & 0xFFFFFF00u) > thr;
                     }
                     const unsigned left = __ballot_sync(kFull, !done);
                     if (__popc(left) <= kCoopLanes) {
-                        jstop = j + 4;
+                        jstop = j + 8;
                         break;
                     }
                 }

@@ -7,11 +7,13 @@
 //
 //   FGY  partial Fisher-Yates on one thread, the displaced entries in a shared
 //        memory hash map.
-//   KPP, MMX  one persistent cooperative kernel: per round every block refreshes
-//        its slice's nearest-centre distances (exact integers); KPP sums w D^2 per
-//        block and every block then finds the sampled colour from the block sums
-//        and the chosen block's slice; MMX takes a packed (D^2, lowest index)
-//        maximum with one atomic per block.  One grid barrier per round.
+//   KPP, MMX  one thread-block cluster (N' up to 16 x 11264) or one persistent
+//        cooperative kernel over the grid: per round every block refreshes its
+//        slice's nearest-centre distances (exact integers); KPP sums w D^2 per
+//        block, every block finds from the block sums the block that holds the
+//        sample, and that block finds the colour in its own slice and posts its
+//        key; MMX takes a packed (D^2, lowest index) maximum with one atomic per
+//        block.  One grid barrier per round.
 //   SFF  one block: subset draw, sort, then minmax over the subset.
 //   VAR  per-chunk value counts and exact weighted moments, then one warp per
 //        group median locates the element of the requested rank.
@@ -104,17 +106,54 @@ constexpr int kFarUnroll = 2;   // groups per warp step in the D^2 update
 
 struct FarShared {
     unsigned long long wsum[kFarWarps];
+    unsigned long long gp[kFarRes / 32];  // k-means++: sums of w D^2 of the slice's 32-colour groups
     uint32_t key;
 };
+
+__device__ __forceinline__ unsigned long long ld_acquire_gpu_u64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_gpu_u64(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Round r's key as posted by the block that holds the sample (slot = key + 2^32),
+// waited for with the limit of the grid barrier; 0xFFFFFFFF if the wait gave up.
+__device__ __forceinline__ uint32_t far_await_key(const unsigned long long *slot, Ctl *ctl, uint64_t limit_ns)
+{
+    uint64_t t0 = 0;
+    for (uint32_t spin = 0;; ++spin) {
+        const unsigned long long v = ld_acquire_gpu_u64(slot);
+        if (v) return (uint32_t)(v & 0xFFFFFFull);
+        __nanosleep(64);
+        if ((spin & 63u) == 63u) {
+            if (ld_acquire_gpu(&ctl->abort)) return 0xFFFFFFFFu;
+            const uint64_t now = globaltimer_ns();
+            if (t0 == 0) t0 = now;
+            else if (now - t0 > limit_ns) {
+                fail(ctl, KQ_ETIMEOUT);
+                atomicExch(&ctl->abort, 1u);
+                return 0xFFFFFFFFu;
+            }
+        }
+    }
+}
 
 // First index i < count whose running sum of vals[0..i] exceeds t, and t minus the
 // sum before it (one warp; every lane returns the same).  Lane l sums the values
 // [l m, l m + m), m = ceil(count / 32), with one round of loads; a warp scan of the
 // lane sums finds the lane, which then walks its own values.  `draw`: t is
 // below(u, total of all values) instead of u itself.
+template <bool kShared = false>
 __device__ __forceinline__ int warp_find(const unsigned long long *vals, int count, bool draw, uint64_t u,
                                          unsigned long long *resid)
 {
+    auto ld = [](const unsigned long long *q) { return kShared ? *q : __ldcg(q); };
     const int lane = threadIdx.x & 31;
     const int m = (count + 31) / 32;
     unsigned long long v[kFindRegs];
@@ -122,12 +161,12 @@ __device__ __forceinline__ int warp_find(const unsigned long long *vals, int cou
 #pragma unroll
     for (int j = 0; j < kFindRegs; ++j) {
         const int i = lane * m + j;
-        v[j] = (j < m && i < count) ? __ldcg(vals + i) : 0ull;
+        v[j] = (j < m && i < count) ? ld(vals + i) : 0ull;
         ls += v[j];
     }
     for (int j = kFindRegs; j < m; ++j) {
         const int i = lane * m + j;
-        if (i < count) ls += __ldcg(vals + i);
+        if (i < count) ls += ld(vals + i);
     }
     unsigned long long x = ls;
     for (int o = 1; o < 32; o <<= 1) {
@@ -152,7 +191,7 @@ __device__ __forceinline__ int warp_find(const unsigned long long *vals, int cou
             }
         }
         for (int j = kFindRegs; !found && j < m; ++j) {
-            const unsigned long long vj = __ldcg(vals + lane * m + j);
+            const unsigned long long vj = ld(vals + lane * m + j);
             if (run + vj > t) {
                 idx = lane * m + j;
                 found = true;
@@ -198,13 +237,50 @@ __device__ uint32_t far_locate(const FarArgs &a, int G, int64_t n, int64_t gstri
     return __shfl_sync(kFull, key, l3 < 0 ? 0 : l3);
 }
 
+// k-means++ sampling when every block keeps its slice in shared memory: every
+// block finds, from the block sums, the block g whose range holds t = below(u,
+// total); block g alone finds the group and the colour in its own shared memory
+// and posts the key to round r's slot, which the other blocks wait for.
+__device__ uint32_t far_locate_owner(const FarArgs &a, FarShared &sh, const uint32_t *s_key, const uint32_t *s_w,
+                                     const uint32_t *s_d2, int G, int b, int cnt, int buf, int r, Ctl *ctl,
+                                     uint64_t limit_ns)
+{
+    const int lane = threadIdx.x & 31;
+    unsigned long long r1, r2;
+    const int g = warp_find(a.part + (size_t)buf * kMaxGrid, G, true, rand64(a.seed, 2, (uint32_t)r), &r1);
+    if (g != b) {
+        uint32_t k = 0u;
+        if (lane == 0) k = far_await_key(a.slot + r, ctl, limit_ns);
+        return __shfl_sync(kFull, k, 0);
+    }
+    const int q = warp_find<true>(sh.gp, (cnt + 31) / 32, false, r1, &r2);
+    const int j = 32 * q + lane;
+    unsigned long long p = 0ull;
+    uint32_t key = 0u;
+    if (j < cnt) {
+        key = s_key[j];
+        p = r == 0 ? (unsigned long long)s_w[j] : (unsigned long long)s_w[j] * s_d2[j];
+    }
+    unsigned long long x = p;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    const int l3 = __ffs(__ballot_sync(kFull, x > r2)) - 1;
+    key = __shfl_sync(kFull, key, l3 < 0 ? 0 : l3);
+    if (lane == 0) st_release_gpu_u64(a.slot + r, (1ull << 32) | key);
+    return key;
+}
+
 // KPP / minmax over the whole grid, for N' above what one cluster holds.  Block b
 // owns a contiguous slice of the unique colours; while a slice fits kFarRes colours
-// the block keeps its keys, weights and D^2 in shared memory for all K rounds (and,
-// for k-means++, also writes D^2 to global memory, where the other blocks read the
-// one group they sample from).  Warps take the slice's 32-colour groups in turn and
-// publish each group's sum of P (k-means++) or fold the packed (D^2, key) maximum
-// into the round's slot (minmax).  One grid barrier per round.
+// the block keeps its keys, weights and D^2 in shared memory for all K rounds, and
+// k-means++ keeps the sums of w D^2 of its 32-colour groups there too: the block
+// that holds a round's sample finds it locally (far_locate_owner).  Larger slices
+// live in global memory, where every block locates the sample (far_locate).  Warps
+// take the slice's groups in turn and sum P per group (k-means++) or fold the
+// packed (D^2, key) maximum into the round's slot (minmax).  One grid barrier per
+// round.
 __global__ void __launch_bounds__(kFarBlock, 1) seed_far(FarArgs a)
 {
     __shared__ FarShared sh;
@@ -283,8 +359,7 @@ __global__ void __launch_bounds__(kFarBlock, 1) seed_far(FarArgs a)
                         const uint32_t md = min(dp[u], key_dist2(key[u], ckey));
                         if (in[u]) {
                             if (res) s_d2[j] = md;
-                            // k-means++ reads the sampled group's D^2 from global memory
-                            if (!res || a.mode == 0) d2[j] = md;
+                            else d2[j] = md;
                         }
                         if (in[u]) pv[u] = a.mode == 0 ? (unsigned long long)wj[u] * md : mmx_pack(md, key[u]);
                     }
@@ -299,7 +374,10 @@ __global__ void __launch_bounds__(kFarBlock, 1) seed_far(FarArgs a)
                         const uint32_t shi = __reduce_add_sync(kFull, (uint32_t)(pv[u] >> 25));
                         const unsigned long long gs = ((unsigned long long)shi << 25) + slo;
                         if (q < ng) {
-                            if (lane == 0) gp[q] = gs;
+                            if (lane == 0) {
+                                if (res) sh.gp[q] = gs;
+                                else gp[q] = gs;
+                            }
                             acc += gs;
                         }
                     }
@@ -321,13 +399,20 @@ __global__ void __launch_bounds__(kFarBlock, 1) seed_far(FarArgs a)
                     const unsigned long long other = __shfl_xor_sync(kFull, acc, o);
                     acc = other > acc ? other : acc;
                 }
-                if (lane == 0 && acc) atomicMax(a.slot + r, acc);
+                if (lane == 0) sh.wsum[warp] = acc;
+                __syncthreads();
+                if (tid == 0) {
+                    unsigned long long mx = 0ull;
+                    for (int k = 0; k < kFarWarps; ++k) mx = sh.wsum[k] > mx ? sh.wsum[k] : mx;
+                    if (mx) atomicMax(a.slot + r, mx);
+                }
             }
         }
         if (!grid_sync(ctl, bar_n, &bar_epoch, limit_ns)) return;
         if (a.mode == 0) {
             if (warp == 0) {
-                const uint32_t k = far_locate(a, G, n, gstride, buf, rand64(a.seed, 2, (uint32_t)r), r == 0);
+                const uint32_t k = res ? far_locate_owner(a, sh, s_key, s_w, s_d2, G, b, cnt, buf, r, ctl, limit_ns)
+                                       : far_locate(a, G, n, gstride, buf, rand64(a.seed, 2, (uint32_t)r), r == 0);
                 if (lane == 0) sh.key = k;
             }
         } else if (tid == 0) {
@@ -336,6 +421,7 @@ __global__ void __launch_bounds__(kFarBlock, 1) seed_far(FarArgs a)
         }
         __syncthreads();
         ckey = sh.key;
+        if (ckey == 0xFFFFFFFFu) return;  // a wait gave up (status KQ_ETIMEOUT)
         if (b == 0 && tid == 0) key_to_centre(a.centers + 3 * r, ckey);
     }
 }
