@@ -293,6 +293,72 @@ KQ_API int kq_batch_tune(const kq_batch_item *h_items, const kq_batch_item *item
                          kq_stream_t stream);
 
 /*
+ * Live batches: images join a launch that is already running.  (The paper treats
+ * one image at a time; this is the serving form of the batched launch above.)
+ * A queue in page-locked host memory (cudaHostAlloc, or a pinned tensor), which
+ * the host and the running kernel both read and write, holds two rings of items,
+ * one per class: class 0 is taken by thread-block clusters of cfg->cluster CTAs,
+ * class 1 by single CTAs (a launch with cluster = 1 serves class 1 only).  The
+ * host publishes an item with kq_live_publish; a group of the running launch
+ * claims it, runs the four steps exactly as kq_batch_run would, and marks it done;
+ * kq_live_done reads the mark.  Per image the results are those of kq_batch_run.
+ *
+ * Memory: every pointer of a live item must be reachable by the running kernel
+ * while it runs.  The item's input pixels must be written by the host thread that
+ * publishes it (or be ordered before the publication by that thread, e.g. by
+ * waiting for a copy's completion), and must not change until the item is done;
+ * its outputs may be read once kq_live_done returns 1.  Buffers of a finished item
+ * may be reused for a later one.
+ *
+ * A live launch exits when the queue is closed and both rings are drained, or after
+ * `idle_us` microseconds without an item to take (a bounded wait: nothing spins
+ * without limit); items published later wait for the next kq_live_run, which
+ * continues from the claim counters in `ws`.  Only one live launch may run on a
+ * queue and its workspace at a time, and no kq_batch_run may share the workspace.
+ */
+typedef struct kq_live_queue {
+    uint32_t tail[2];       /* items published per class (written by kq_live_publish) */
+    uint32_t closed;        /* 1 after kq_live_close */
+    uint32_t capacity;      /* ring slots per class */
+    uint32_t reserved[12];
+    /* followed by kq_batch_item items[2][capacity] and uint32_t done[2][capacity] */
+} kq_live_queue;
+
+/* Bytes of a live queue with `capacity` ring slots per class (0 for capacity < 1). */
+KQ_API size_t kq_live_bytes(int32_t capacity);
+
+/* Host: empties the queue at `q` (kq_live_bytes(capacity) bytes of page-locked
+ * host memory). */
+KQ_API int kq_live_init(kq_live_queue *q, int32_t capacity);
+
+/* Zeroes the claim counters of a live queue in the batch workspace `ws` (asynchronous
+ * on `stream`); call it once for a freshly initialised queue, before its first
+ * kq_live_run. */
+KQ_API int kq_live_reset(void *ws, size_t ws_bytes, kq_stream_t stream);
+
+/* Host: publishes a copy of *item (host memory) in class `cls` and returns its
+ * sequence number in *h_seq.  KQ_ECAPACITY when the ring slot it needs still holds
+ * an item that is not done; KQ_EINVAL for an invalid item, as kq_batch_plan checks
+ * them, or after kq_live_close. */
+KQ_API int kq_live_publish(kq_live_queue *q, int32_t cls, const kq_batch_item *item, int64_t *h_seq);
+
+/* Host: 1 when item `seq` of class `cls` is done (its outputs are written), else 0.
+ * The mark lives in the item's ring slot: once a later item is published into the
+ * same slot (which kq_live_publish allows only after this one is done), the call
+ * answers for that item instead, so read it before publishing `capacity` more items
+ * of the class. */
+KQ_API int kq_live_done(const kq_live_queue *q, int32_t cls, int64_t seq);
+
+/* Host: no more items will be published; the running launch exits once drained. */
+KQ_API int kq_live_close(kq_live_queue *q);
+
+/* Launches the persistent live kernel on `stream` (asynchronous): cfg->cluster
+ * CTAs per group for class 0 (cfg->split_pixels is not used: the publisher picks
+ * the class), idle limit `idle_us` (>= 1). */
+KQ_API int kq_live_run(kq_live_queue *q, const kq_batch_config *cfg, uint32_t idle_us, void *ws, size_t ws_bytes,
+                       kq_stream_t stream);
+
+/*
  * kq_lloyd without a workspace (the paper has no counterpart: this entry point
  * exists for callers of this library that cannot allocate device memory -- for
  * example a plug-in inside a host application that owns the whole device memory

@@ -17,6 +17,7 @@
 // FP32 summation order of the SSE, whose block partition differs.
 #include <math.h>
 #include <stddef.h>
+#include <string.h>
 
 #include <algorithm>
 #include <mutex>
@@ -50,6 +51,8 @@ struct SlotMisc {
     uint32_t gcnt[3 * 256];
     int quota[2 * kDenCells];
     int32_t item;
+    int32_t live_busy;        // live launches: a CTA of the cluster ran a single-CTA item
+    long long live_dec;       // live launches: rank 0's decision for the cluster
     uint8_t lbg_pal[3 * kMaxK];
 };
 
@@ -72,6 +75,7 @@ constexpr size_t kDynSff = sizeof(uint32_t) * (2 * kMapSlots + 2 * kSffMax);
 constexpr size_t kDynRows = sizeof(uint32_t) * (size_t)kMaxK * kRowStride + sizeof(float) * kChunkSlots;
 constexpr size_t kDynBytes = kDynSff > kDynFgy ? (kDynSff > kDynRows ? kDynSff : kDynRows)
                                                : (kDynFgy > kDynRows ? kDynFgy : kDynRows);
+static_assert(sizeof(WuShared) <= kDynBytes, "the Wu split state fits the dynamic shared memory");
 
 struct BatchShared {
     unsigned long long scan[kBW];
@@ -798,7 +802,9 @@ __device__ void group_seed(Group &g, const kq_batch_item &it, int64_t n, BatchSh
         group_lbg(g, it, n, bs, sh, dyn, status);
         break;
     case KQ_INIT_WU: {
-        __shared__ WuShared wsh;
+        // the split state in the step's dynamic shared memory (no other step's
+        // data is live there during the seeding)
+        WuShared &wsh = *reinterpret_cast<WuShared *>(dyn);
         unsigned long long *cell = g.at_slot<unsigned long long>(kSoWu);
         unsigned long long *cum = cell + 5 * (size_t)kWuCells;
         if (g.rank == 0)
@@ -968,6 +974,180 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(BatchArgs a)
     }
 }
 
+// ---------------------------------------------------------------- live batches
+// The queue lives in page-locked host memory: the host publishes items (release
+// stores of the tails) while the kernel runs; groups claim them through counters
+// in the workspace header and post each item's done mark with a release store.
+constexpr size_t kLiveHeadOff = 64;  // the two claim counters in the workspace header
+constexpr long long kLiveSingles = -1, kLiveExit = -2;
+
+struct LiveArgs {
+    const kq_live_queue *q;
+    const kq_batch_item *items;  // [2][cap]
+    uint32_t *done;              // [2][cap]
+    uint32_t cap;
+    uint32_t *head;              // [2] claims (device memory)
+    int32_t C;
+    uint64_t idle_ns;
+    char *slots;
+};
+
+__device__ __forceinline__ uint32_t ld_acquire_sys_u32(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_sys_u32(uint32_t *p, uint32_t v)
+{
+    asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Items published in class c and not yet claimed.
+__device__ __forceinline__ bool live_pending(const LiveArgs &a, int c)
+{
+    const uint32_t t = ld_acquire_sys_u32(&a.q->tail[c]);
+    return (int32_t)(t - *(volatile const uint32_t *)&a.head[c]) > 0;
+}
+
+// Claims the oldest unclaimed item of class c: its sequence number, or -1.
+__device__ long long live_claim(const LiveArgs &a, int c)
+{
+    for (;;) {
+        const uint32_t t = ld_acquire_sys_u32(&a.q->tail[c]);
+        const uint32_t h = *(volatile const uint32_t *)&a.head[c];
+        if ((int32_t)(t - h) <= 0) return -1;
+        if (atomicCAS(&a.head[c], h, h + 1u) == h) return (long long)h;
+    }
+}
+
+// Rank 0 of a cluster: a class-0 item to run, kLiveSingles while class-1 items
+// wait, or kLiveExit once the queue is closed and drained or nothing came for the
+// idle limit (measured from `last`, the group's last item).
+__device__ long long live_decide(const LiveArgs &a, uint64_t last)
+{
+    for (;;) {
+        const long long j = live_claim(a, 0);
+        if (j >= 0) return j;
+        if (live_pending(a, 1)) return kLiveSingles;
+        if (ld_acquire_sys_u32(&a.q->closed) && !live_pending(a, 0) && !live_pending(a, 1)) return kLiveExit;
+        if (globaltimer_ns() - last > a.idle_ns) return kLiveExit;
+        __nanosleep(2000);
+    }
+}
+
+// A class-1 item for a CTA on its own, or -1 (cluster launches: none waiting, or
+// a class-0 item waits); single-CTA launches wait for one up to the idle limit
+// and return kLiveExit after it, or once the queue is closed and drained.
+__device__ long long live_next_single(const LiveArgs &a, uint64_t last)
+{
+    if (a.C > 1) return live_pending(a, 0) ? -1 : live_claim(a, 1);
+    for (;;) {
+        const long long k = live_claim(a, 1);
+        if (k >= 0) return k;
+        if (ld_acquire_sys_u32(&a.q->closed) && !live_pending(a, 1)) return kLiveExit;
+        if (globaltimer_ns() - last > a.idle_ns) return kLiveExit;
+        __nanosleep(2000);
+    }
+}
+
+// The item of class c and sequence number seq, copied to shared memory (thread 0).
+__device__ __forceinline__ void live_load(const LiveArgs &a, int c, uint32_t seq, kq_batch_item *dst)
+{
+    const unsigned long long *src =
+        reinterpret_cast<const unsigned long long *>(a.items + (size_t)c * a.cap + seq % a.cap);
+    unsigned long long *d = reinterpret_cast<unsigned long long *>(dst);
+    for (int i = 0; i < (int)(sizeof(kq_batch_item) / 8); ++i) d[i] = __ldcv(src + i);
+}
+
+__device__ __forceinline__ void live_mark(const LiveArgs &a, int c, uint32_t seq)
+{
+    __threadfence_system();
+    st_release_sys_u32(a.done + (size_t)c * a.cap + seq % a.cap, seq + 1u);
+}
+
+__global__ void __launch_bounds__(kBT, 1) batch_live_kernel(LiveArgs a)
+{
+    __shared__ LloydShared sh;
+    __shared__ BatchShared bs;
+    __shared__ kq_batch_item s_item;
+    __shared__ long long s_dec;
+    extern __shared__ __align__(16) uint32_t dyn[];
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int rank = a.C > 1 ? (int)cluster_ctarank() : 0;
+    Group gc{a.C, rank, a.slots + (size_t)(blockIdx.x - rank) * kSlotBytes};
+    Group g1{1, 0, a.slots + (size_t)blockIdx.x * kSlotBytes};
+    SlotMisc *ms = gc.misc();
+    kq_batch_item *item = &s_item;
+    uint64_t last = globaltimer_ns();
+    // Lane 0 of warp 0 polls the queue; the rest of warp 0 waits for it in a
+    // __shfl_sync, so that the warp reaches every block or cluster barrier
+    // converged (an aligned barrier needs all of a warp's threads at once).
+    for (;;) {
+        if (a.C > 1) {
+            if (rank == 0 && tid < 32) {
+                long long d = 0;
+                if (lane == 0) {
+                    if (atomicExch(&ms->live_busy, 0)) last = globaltimer_ns();
+                    d = live_decide(a, last);
+                    ms->live_dec = d;
+                }
+                d = __shfl_sync(0xffffffffu, d, 0);
+            }
+            gc();
+            const long long dec = __ldcg(&ms->live_dec);
+            gc();
+            if (dec == kLiveExit) return;
+            if (dec >= 0) {
+                __threadfence();
+                if (tid == 0) live_load(a, 0, (uint32_t)dec, item);
+                __syncwarp();
+                __syncthreads();
+                run_item(gc, *item, bs, sh, dyn);
+                gc();
+                if (rank == 0 && tid == 0) {
+                    live_mark(a, 0, (uint32_t)dec);
+                    last = globaltimer_ns();
+                }
+                __syncwarp();
+                continue;
+            }
+        }
+        // class-1 items, one CTA each
+        bool ran = false;
+        for (;;) {
+            if (tid < 32) {
+                long long d = 0;
+                if (lane == 0) {
+                    d = live_next_single(a, last);
+                    s_dec = d;
+                }
+                d = __shfl_sync(0xffffffffu, d, 0);
+            }
+            __syncthreads();
+            const long long k = s_dec;
+            __syncthreads();
+            if (k == kLiveExit) return;
+            if (k < 0) break;
+            __threadfence();
+            if (tid == 0) live_load(a, 1, (uint32_t)k, item);
+            __syncwarp();
+            __syncthreads();
+            run_item(g1, *item, bs, sh, dyn);
+            __syncthreads();
+            if (tid == 0) {
+                live_mark(a, 1, (uint32_t)k);
+                last = globaltimer_ns();
+            }
+            __syncwarp();
+            ran = true;
+        }
+        if (a.C > 1 && ran && tid == 0) atomicExch(&ms->live_busy, 1);
+        __syncwarp();
+    }
+}
+
 // ---------------------------------------------------------------- host side
 struct BatchDev {
     bool done = false;
@@ -1127,6 +1307,117 @@ extern "C" KQ_API int kq_batch_run(const kq_batch_item *items, int32_t n_items, 
     lc.attrs = attr;
     lc.numAttrs = C > 1 ? 1 : 0;
     return cudaLaunchKernelEx(&lc, batch_kernel, a) == cudaSuccess ? KQ_OK : KQ_ECUDA;
+}
+
+extern "C" KQ_API size_t kq_live_bytes(int32_t capacity)
+{
+    if (capacity < 1) return 0;
+    return sizeof(kq_live_queue) + 2 * (size_t)capacity * (sizeof(kq_batch_item) + sizeof(uint32_t));
+}
+
+static kq_batch_item *live_items(kq_live_queue *q) { return reinterpret_cast<kq_batch_item *>(q + 1); }
+static uint32_t *live_done(kq_live_queue *q)
+{
+    return reinterpret_cast<uint32_t *>(live_items(q) + 2 * (size_t)q->capacity);
+}
+
+extern "C" KQ_API int kq_live_init(kq_live_queue *q, int32_t capacity)
+{
+    if (!q || capacity < 1) return KQ_EINVAL;
+    memset(q, 0, kq_live_bytes(capacity));
+    q->capacity = (uint32_t)capacity;
+    __atomic_thread_fence(__ATOMIC_SEQ_CST);
+    return KQ_OK;
+}
+
+extern "C" KQ_API int kq_live_reset(void *ws, size_t ws_bytes, kq_stream_t stream)
+{
+    if (!ws || ws_bytes < kHeaderBytes || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0) return KQ_EINVAL;
+    return cudaMemsetAsync(static_cast<char *>(ws) + kLiveHeadOff, 0, 2 * sizeof(uint32_t), (cudaStream_t)stream) ==
+                   cudaSuccess
+               ? KQ_OK
+               : KQ_ECUDA;
+}
+
+extern "C" KQ_API int kq_live_publish(kq_live_queue *q, int32_t cls, const kq_batch_item *item, int64_t *h_seq)
+{
+    if (!q || !item || !h_seq || (cls != 0 && cls != 1) || q->capacity < 1) return KQ_EINVAL;
+    if (__atomic_load_n(&q->closed, __ATOMIC_ACQUIRE) || !host_item_ok(*item)) return KQ_EINVAL;
+    const uint32_t cap = q->capacity;
+    const uint32_t t = __atomic_load_n(&q->tail[cls], __ATOMIC_RELAXED);
+    uint32_t *done = live_done(q) + (size_t)cls * cap;
+    const uint32_t slot = t % cap;
+    // the slot's previous item (t - cap) must be done before it is overwritten
+    if (t >= cap && __atomic_load_n(&done[slot], __ATOMIC_ACQUIRE) != t - cap + 1u) return KQ_ECAPACITY;
+    live_items(q)[(size_t)cls * cap + slot] = *item;
+    __atomic_store_n(&done[slot], 0u, __ATOMIC_RELAXED);
+    __atomic_store_n(&q->tail[cls], t + 1u, __ATOMIC_RELEASE);
+    *h_seq = (int64_t)t;
+    return KQ_OK;
+}
+
+extern "C" KQ_API int kq_live_done(const kq_live_queue *q, int32_t cls, int64_t seq)
+{
+    if (!q || (cls != 0 && cls != 1) || seq < 0 || q->capacity < 1) return 0;
+    const uint32_t cap = q->capacity;
+    const uint32_t *done = live_done(const_cast<kq_live_queue *>(q)) + (size_t)cls * cap;
+    return __atomic_load_n(&done[(uint32_t)seq % cap], __ATOMIC_ACQUIRE) == (uint32_t)seq + 1u ? 1 : 0;
+}
+
+extern "C" KQ_API int kq_live_close(kq_live_queue *q)
+{
+    if (!q) return KQ_EINVAL;
+    __atomic_store_n(&q->closed, 1u, __ATOMIC_RELEASE);
+    return KQ_OK;
+}
+
+extern "C" KQ_API int kq_live_run(kq_live_queue *q, const kq_batch_config *cfg, uint32_t idle_us, void *ws,
+                                  size_t ws_bytes, kq_stream_t stream)
+{
+    if (!q || !cfg || !ws || idle_us < 1 || q->capacity < 1) return KQ_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(ws) & 255u) != 0) return KQ_EINVAL;
+    const int C = cfg->cluster;
+    if (C < 1 || C > kMaxCluster || (C & (C - 1))) return KQ_EINVAL;
+    const BatchDev *d = batch_dev();
+    if (!d) return KQ_ECUDA;
+    if (C > d->max_cluster || (C > 1 && d->clusters[C] < 1)) return KQ_EINVAL;
+    const int grid = grid_for(*d, C);
+    if (ws_bytes < kHeaderBytes + (size_t)grid * kSlotBytes) return KQ_ENOMEM;
+    // the queue must be page-locked host memory that the device can reach
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, q) != cudaSuccess || pa.type != cudaMemoryTypeHost || !pa.devicePointer) {
+        cudaGetLastError();
+        return KQ_EINVAL;
+    }
+    void *dq = pa.devicePointer;
+    kq_live_queue *qd = static_cast<kq_live_queue *>(dq);
+    LiveArgs a;
+    a.q = qd;
+    a.items = live_items(qd);
+    a.cap = q->capacity;
+    a.done = reinterpret_cast<uint32_t *>(live_items(qd) + 2 * (size_t)a.cap);
+    a.head = reinterpret_cast<uint32_t *>(static_cast<char *>(ws) + kLiveHeadOff);
+    a.C = C;
+    a.idle_ns = (uint64_t)idle_us * 1000ull;
+    a.slots = static_cast<char *>(ws) + kHeaderBytes;
+    if (cudaFuncSetAttribute((const void *)batch_live_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kDynBytes) != cudaSuccess)
+        return KQ_ECUDA;
+    cudaFuncSetAttribute((const void *)batch_live_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaGetLastError();
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(grid);
+    lc.blockDim = dim3(kBT);
+    lc.dynamicSmemBytes = kDynBytes;
+    lc.stream = (cudaStream_t)stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    lc.attrs = attr;
+    lc.numAttrs = C > 1 ? 1 : 0;
+    return cudaLaunchKernelEx(&lc, batch_live_kernel, a) == cudaSuccess ? KQ_OK : KQ_ECUDA;
 }
 
 extern "C" KQ_API int kq_batch_tune(const kq_batch_item *h_items, const kq_batch_item *items, int32_t n_items,

@@ -383,7 +383,7 @@ __device__ __forceinline__ WuMom wu_vol(const unsigned long long *cum, const int
     const unsigned long long *c111 = cum + 5 * (size_t)wu_cidx(hi[0], hi[1], hi[2]);
 #pragma unroll
     for (int j = 0; j < 5; ++j)
-        v[j] = c111[j] - c110[j] - c101[j] + c100[j] - c011[j] + c010[j] + c001[j] - c000[j];
+        v[j] = __ldcg(c111 + j) - __ldcg(c110 + j) - __ldcg(c101 + j) + __ldcg(c100 + j) - __ldcg(c011 + j) + __ldcg(c010 + j) + __ldcg(c001 + j) - __ldcg(c000 + j);
     m.w = v[0];
     m.s[0] = v[1];
     m.s[1] = v[2];
@@ -460,7 +460,7 @@ __device__ __forceinline__ void wu_cum_lines(unsigned long long *cum, int step, 
         for (int h = 0; h < 2; ++h) {
             unsigned long long v[16];
 #pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] = c[5 * (1 + 16 * h + i) * st];
+            for (int i = 0; i < 16; ++i) v[i] = __ldcg(c + 5 * (1 + 16 * h + i) * st);
             v[0] += carry;
 #pragma unroll
             for (int i = 1; i < 16; ++i) v[i] += v[i - 1];
@@ -471,7 +471,10 @@ __device__ __forceinline__ void wu_cum_lines(unsigned long long *cum, int step, 
     }
 }
 
-// All four steps by one block (all its threads).
+// All four steps by one block (all its threads).  The moments written by other
+// threads are read from L2 (__ldcg) throughout: through L1 the second and third
+// steps were seen to read stale lines in a persistent kernel that runs many
+// images on one SM.
 __device__ void wu_cumulate_block(const unsigned long long *cell, unsigned long long *cum)
 {
     wu_cum_copy(cell, cum, threadIdx.x, blockDim.x);

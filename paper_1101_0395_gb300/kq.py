@@ -88,6 +88,13 @@ _SIGS = {
     "kq_batch_run": (C.c_int, [_vp, C.c_int32, _vp, C.c_int32, _vp, _vp, C.c_size_t, _vp]),
     "kq_batch_tune": (C.c_int, [_vp, _vp, C.c_int32, _vp, _vp, C.POINTER(C.c_int32), C.POINTER(C.c_float), _vp,
                                 C.c_size_t, _vp]),
+    "kq_live_bytes": (C.c_size_t, [C.c_int32]),
+    "kq_live_init": (C.c_int, [_vp, C.c_int32]),
+    "kq_live_reset": (C.c_int, [_vp, C.c_size_t, _vp]),
+    "kq_live_publish": (C.c_int, [_vp, C.c_int32, _vp, C.POINTER(C.c_int64)]),
+    "kq_live_done": (C.c_int, [_vp, C.c_int32, C.c_int64]),
+    "kq_live_close": (C.c_int, [_vp]),
+    "kq_live_run": (C.c_int, [_vp, _vp, C.c_uint32, _vp, C.c_size_t, _vp]),
 }
 
 
@@ -415,6 +422,51 @@ def kq_batch_tune(h_items: np.ndarray, items: torch.Tensor, order: torch.Tensor,
                                                 C.byref(cfg), C.byref(nb), C.byref(ms), _ptr(ws),
                                                 ws.numel() * ws.element_size(), _stream(stream)))
     return cfg, int(nb.value), float(ms.value)
+
+
+class LiveQueue:
+    """The queue of a live batch launch (kq_live_* in include/kq.h): a page-locked
+    host buffer that the host publishes items into and the running kernel claims
+    them from.  `capacity` ring slots per class; class 0 goes to thread-block
+    clusters, class 1 to single CTAs."""
+
+    def __init__(self, capacity: int):
+        self.capacity = int(capacity)
+        nbytes = int(lib().kq_live_bytes(self.capacity))
+        if nbytes == 0:
+            raise ValueError("capacity must be >= 1")
+        self.buf = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+        self.ptr = self.buf.data_ptr()
+        _check("kq_live_init", lib().kq_live_init(self.ptr, self.capacity))
+
+    def publish(self, cls: int, item: np.ndarray) -> Optional[int]:
+        """Publishes one item (a BATCH_ITEM_DTYPE record); its sequence number, or
+        None while the ring slot it needs still holds an unfinished item."""
+        rec = np.ascontiguousarray(np.asarray(item, dtype=BATCH_ITEM_DTYPE).reshape(1))
+        seq = C.c_int64(-1)
+        st = lib().kq_live_publish(self.ptr, int(cls), rec.ctypes.data, C.byref(seq))
+        if st == KQ_ECAPACITY:
+            return None
+        _check("kq_live_publish", st)
+        return int(seq.value)
+
+    def done(self, cls: int, seq: int) -> bool:
+        return lib().kq_live_done(self.ptr, int(cls), int(seq)) == 1
+
+    def close(self) -> None:
+        _check("kq_live_close", lib().kq_live_close(self.ptr))
+
+    def tails(self):
+        return tuple(int(v) for v in self.buf[:8].numpy().view(np.uint32))
+
+
+def kq_live_reset(ws: torch.Tensor, stream=None) -> None:
+    _check("kq_live_reset", lib().kq_live_reset(_ptr(ws), ws.numel() * ws.element_size(), _stream(stream)))
+
+
+def kq_live_run(q: LiveQueue, cfg: BatchConfig, idle_us: int, ws: torch.Tensor, stream=None) -> None:
+    _check("kq_live_run", lib().kq_live_run(q.ptr, C.byref(cfg), int(idle_us), _ptr(ws),
+                                            ws.numel() * ws.element_size(), _stream(stream)))
 
 
 def _align(v: int, a: int = 256) -> int:

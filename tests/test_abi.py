@@ -18,7 +18,9 @@ def test_exports_every_declared_symbol():
                           "kq_batch_scratch_bytes", "kq_batch_workspace_size", "kq_batch_max_cluster",
                           "kq_batch_plan", "kq_batch_run", "kq_batch_tune", "kq_pixel_keys",
                           "kq_histogram_strided", "kq_set_wait_limit", "kq_map_ndc_read",
-                          "kq_lab_points", "kq_seed_points", "kq_lloyd_points", "kq_lab_palette", "kq_map_labels"}
+                          "kq_lab_points", "kq_seed_points", "kq_lloyd_points", "kq_lab_palette", "kq_map_labels",
+                              "kq_live_bytes", "kq_live_init", "kq_live_reset", "kq_live_publish", "kq_live_done",
+                              "kq_live_close", "kq_live_run"}
     L = kq.lib()
     for n in names:
         assert getattr(L, n) is not None
