@@ -624,6 +624,8 @@ EXTRA_BATCH = 64            # every 8th image, by size, of the 512-image batch s
 EXTRA_SERVE_POOL = 12       # serving: images the requests pick from
 EXTRA_SERVE_RATE = 200.0    # req/s
 EXTRA_SERVE_SECONDS = 3.0
+EXTRA_OVERLOAD_RATE = 2000.0  # req/s: a short overload, where throughput counts
+EXTRA_OVERLOAD_SECONDS = 1.0
 
 
 def _gen_workload_image(args):
@@ -837,7 +839,51 @@ def extra_serving(pool, imgs, dev) -> dict:
     reqs = requests()
     out = serve.run_trace(srv, reqs)
     waves, solo = srv.waves, srv.backend.solo_waves
-    del srv
+
+    def live_server():
+        be = serve.LiveBackend(cluster, split, device=dev, idle_us=20000, capacity=4096)
+        return serve.LiveServer(be, 16 << 30, 2 << 30), be
+
+    lsrv, lbe = live_server()
+    for r in requests(8):
+        lsrv.submit(r)
+    lsrv.drain()
+    lsrv.finished.clear()
+    lreqs = requests()
+    lout = serve.run_trace(lsrv, lreqs)
+    lsame = sum(int(a.result["sse_num"]) == int(b.result["sse_num"]) for a, b in zip(reqs, lreqs))
+
+    # overload: the same request mix arriving 10x faster, through the wave server,
+    # the live server and one offline batch of the same images
+    oarr = serve.poisson_arrivals(EXTRA_OVERLOAD_RATE, EXTRA_OVERLOAD_SECONDS, 4102)
+
+    def oreqs():
+        return [serve.Request(rid=i, rgb=h_imgs[int(picks[i % len(picks)])], K=int(ks[i % len(ks)]), scheme=SCHEME,
+                              seed=1000 + i, arrival=float(oarr[i])) for i in range(oarr.size)]
+    wo = serve.run_trace(srv, oreqs())
+    lo_reqs = oreqs()
+    lo = serve.run_trace(lsrv, lo_reqs)
+    llaunches = lbe.launches
+    lbe.close()
+    del srv, lsrv, lbe
+    torch.cuda.empty_cache()
+    ob = oreqs()[:256]  # the first 256 requests of the same mix
+    bq = kq.BatchQuantizer([r.rgb.numel() // 3 for r in ob], [r.K for r in ob], SCHEME, [r.seed for r in ob],
+                           device=dev)
+    for i, r in enumerate(ob):
+        bq.rgb(i).copy_(r.rgb)
+    bq.plan(kq.BatchConfig(cluster, 0, split))
+    bq.run()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    bq.run()
+    t1.record()
+    torch.cuda.synchronize()
+    ob_ms = t0.elapsed_time(t1)
+    ob_px = sum(r.rgb.numel() // 3 for r in ob)
+    del bq
     torch.cuda.empty_cache()
     plain = serve.Server(serve.PlainBackend(max_px, device=dev), 1 << 30, streams=1, max_wave=1)
     for r in requests(4):
@@ -853,6 +899,17 @@ def extra_serving(pool, imgs, dev) -> dict:
             "requests": len(reqs),
             "server": {"p50_ms": out["p50_ms"], "p99_ms": out["p99_ms"], "img_per_s": out["img_per_s"],
                        "mpix_per_s": out["mpix_per_s"], "waves": waves, "solo_waves": solo},
+            "live_server": {"p50_ms": lout["p50_ms"], "p99_ms": lout["p99_ms"], "img_per_s": lout["img_per_s"],
+                            "mpix_per_s": lout["mpix_per_s"], "same_sse_requests": lsame},
+            "overload": {"workload": "the same mix at %g req/s for %g s (%d requests)"
+                                     % (EXTRA_OVERLOAD_RATE, EXTRA_OVERLOAD_SECONDS, oarr.size),
+                         "server": {"p50_ms": wo["p50_ms"], "p99_ms": wo["p99_ms"], "img_per_s": wo["img_per_s"],
+                                    "mpix_per_s": wo["mpix_per_s"]},
+                         "live_server": {"p50_ms": lo["p50_ms"], "p99_ms": lo["p99_ms"], "img_per_s": lo["img_per_s"],
+                                         "mpix_per_s": lo["mpix_per_s"], "launches": llaunches},
+                         "offline_batch": {"images": len(ob), "ms": ob_ms, "mpix_per_s": ob_px / ob_ms / 1e3,
+                                           "img_per_s": len(ob) / ob_ms * 1e3,
+                                           "note": "the first 256 requests as one kq_batch_run, inputs resident"}},
             "plain_server": {"p50_ms": pout["p50_ms"], "p99_ms": pout["p99_ms"], "img_per_s": pout["img_per_s"],
                              "mpix_per_s": pout["mpix_per_s"]},
             "same_sse_requests": same}

@@ -24,6 +24,13 @@ as its queue empties and the new launch's blocks take their SMs.  Each image is
 computed by one block group with no data shared with other images, so a
 request's result does not depend on what else is in the batch.
 
+``LiveServer`` admits requests into a launch that is already running
+(kq_live_*): each admitted request is published into the launch's queue at
+once, a group of the persistent kernel takes it as soon as one is free, and the
+host retires it when its done mark appears.  Nothing waits for a wave to drain.
+Its pixels and outputs stay in page-locked host memory, which the kernel reads
+and writes directly; the colour lists and scratch come from a device pool.
+
 The device side sits behind a small backend interface so that the scheduling
 logic can be exercised without a GPU.
 """
@@ -112,6 +119,9 @@ class Request:
     block: int = -1
     layout: Dict[str, Tuple[int, int]] = field(default_factory=dict)
     nbytes: int = 0
+    dev_block: int = -1                                   # LiveServer: device pool block
+    dev_layout: Dict[str, Tuple[int, int]] = field(default_factory=dict)
+    dev_bytes: int = 0
     admitted: float = -1.0
     done: float = -1.0
     idx: Optional[np.ndarray] = None
@@ -224,6 +234,113 @@ class Server:
 
     def idle(self) -> bool:
         return not self.waiting and not self.running
+
+    def drain(self, poll_s: float = 0.0) -> None:
+        while not self.idle():
+            if self.step() == 0 and poll_s > 0:
+                time.sleep(poll_s)
+
+
+LIVE_HOST = ("rgb", "idx", "centers", "palette", "result")
+LIVE_DEV = ("keys", "weights", "labels", "scratch")
+
+
+def live_layout(n_pixels: int, K: int, scratch_bytes, pixels_in_place: bool):
+    """Offsets and sizes of a live request's buffers: (host block, device block).
+    With pixels_in_place the request's own page-locked pixels are used as they are."""
+    cap = max(0, min(int(n_pixels), 1 << 24))
+    sizes = {"rgb": 0 if pixels_in_place else 3 * n_pixels, "idx": n_pixels, "centers": 24 * K, "palette": 3 * K,
+             "result": RESULT_BYTES, "keys": 4 * cap, "weights": 4 * cap, "labels": cap,
+             "scratch": scratch_bytes(cap)}
+    host, dev, ho, do = {}, {}, 0, 0
+    for name in LIVE_HOST:
+        host[name] = (ho, sizes[name])
+        ho = _align(ho + max(sizes[name], 1))
+    for name in LIVE_DEV:
+        dev[name] = (do, sizes[name])
+        do = _align(do + max(sizes[name], 1))
+    return host, ho, dev, do
+
+
+class LiveServer:
+    """Continuous admission into a running launch (see the module docstring).
+
+    step() retires every request whose done mark is set, then admits waiting
+    requests in arrival order while their host and device blocks fit and the
+    queue has a free slot (the first that does not fit waits; nobody overtakes
+    it), publishing each at once, and keeps a launch running while requests are
+    in flight (the launch leaves by itself after an idle limit)."""
+
+    def __init__(self, backend, pool_bytes: int, host_bytes: int, clock=time.perf_counter):
+        self.backend = backend
+        self.dev_arena = Arena(pool_bytes)
+        self.host_arena = Arena(host_bytes)
+        self.clock = clock
+        self.t0 = clock()
+        backend.setup(pool_bytes, host_bytes)
+        self.waiting: Deque[Request] = deque()
+        self.inflight: Dict[Tuple[int, int], Request] = {}
+        self.finished: List[Request] = []
+        self.max_inflight = 0
+
+    def now(self) -> float:
+        return self.clock() - self.t0
+
+    def submit(self, req: Request) -> None:
+        npx = req.rgb.numel() if hasattr(req.rgb, "numel") else req.rgb.size
+        req.n_pixels = int(npx // 3)
+        in_place = self.backend.pixels_in_place(req)
+        req.layout, req.nbytes, req.dev_layout, req.dev_bytes = live_layout(req.n_pixels, req.K,
+                                                                              self.backend.scratch_bytes, in_place)
+        if req.nbytes > self.host_arena.size or req.dev_bytes > self.dev_arena.size:
+            raise ValueError("request %d does not fit the pools" % req.rid)
+        self.waiting.append(req)
+
+    def _retire(self, key, t) -> None:
+        r = self.inflight.pop(key)
+        self.backend.collect(r)
+        r.done = t
+        self.host_arena.release(r.block)
+        self.dev_arena.release(r.dev_block)
+        self.finished.append(r)
+
+    def step(self) -> int:
+        """Retires finished requests and admits new ones; returns requests completed."""
+        t = self.now()
+        done_keys = [k for k in self.inflight if self.backend.done(*k)]
+        for k in done_keys:
+            self._retire(k, t)
+        while self.waiting:
+            r = self.waiting[0]
+            hb = self.host_arena.alloc(r.nbytes)
+            if hb is None:
+                break
+            db = self.dev_arena.alloc(r.dev_bytes)
+            if db is None:
+                self.host_arena.release(hb)
+                break
+            r.block, r.dev_block = hb, db
+            key = self.backend.publish(r)
+            if key is None:  # no free queue slot
+                self.host_arena.release(hb)
+                self.dev_arena.release(db)
+                break
+            self.waiting.popleft()
+            r.admitted = self.now()
+            # the slot's previous item was done (publication checks that) and its
+            # mark is gone with it: retire it now if it is still listed
+            prev = (key[0], key[1] - self.backend.capacity)
+            if prev in self.inflight:
+                self._retire(prev, self.now())
+                done_keys.append(prev)
+            self.inflight[key] = r
+            self.max_inflight = max(self.max_inflight, len(self.inflight))
+        if self.inflight:
+            self.backend.ensure_running()
+        return len(done_keys)
+
+    def idle(self) -> bool:
+        return not self.waiting and not self.inflight
 
     def drain(self, poll_s: float = 0.0) -> None:
         while not self.idle():
@@ -475,3 +592,92 @@ class PlainBackend:
             res["n_unique"] = int(hs[7296:7300].view(np.int32)[0])
             res["status"] = res["lloyd"]["status"]
             r.result = res
+
+
+class LiveBackend:
+    """The device side of LiveServer: a page-locked host pool (pixels unless the
+    request's own are page-locked, indices, centres, palette, result), a device
+    pool (colour lists, scratch), one batch workspace and the queue of one live
+    launch (kq_live_run), relaunched whenever requests are in flight and the last
+    launch has left after its idle limit."""
+
+    def __init__(self, cluster: int = 1, split_pixels: int = 1 << 62, device=None, idle_us: int = 20000,
+                 capacity: int = 1024):
+        import torch
+
+        from . import kq
+
+        self.torch, self.kq = torch, kq
+        self.device = torch.device("cuda") if device is None else torch.device(device)
+        self.cfg = kq.BatchConfig(int(cluster), 0, int(split_pixels))
+        self.split = int(split_pixels) if int(cluster) > 1 else 1 << 62
+        self.idle_us = int(idle_us)
+        self.capacity = int(capacity)
+        self.launches = 0
+
+    def scratch_bytes(self, cap: int) -> int:
+        return self.kq.kq_batch_scratch_bytes(cap)
+
+    def pixels_in_place(self, r: Request) -> bool:
+        t = r.rgb
+        return hasattr(t, "is_pinned") and t.is_pinned() and t.is_contiguous()
+
+    def setup(self, pool_bytes: int, host_bytes: int) -> None:
+        torch, kq = self.torch, self.kq
+        self.pool = torch.empty(pool_bytes, dtype=torch.uint8, device=self.device)
+        self.host = torch.empty(host_bytes, dtype=torch.uint8).pin_memory()
+        self.ws = torch.zeros(kq.kq_batch_workspace_size(), dtype=torch.uint8, device=self.device)
+        self.q = kq.LiveQueue(self.capacity)
+        kq.kq_live_reset(self.ws)
+        self.stream = torch.cuda.Stream(device=self.device)
+        self.ev = None
+        torch.cuda.synchronize(self.device)
+
+    def ensure_running(self) -> None:
+        if self.ev is None or self.ev.query():
+            self.kq.kq_live_run(self.q, self.cfg, self.idle_us, self.ws, stream=self.stream)
+            self.ev = self.torch.cuda.Event()
+            self.ev.record(self.stream)
+            self.launches += 1
+
+    def publish(self, r: Request):
+        kq = self.kq
+        hb, db = self.host.data_ptr() + r.block, self.pool.data_ptr() + r.dev_block
+        it = np.zeros(1, dtype=kq.BATCH_ITEM_DTYPE)
+        for name in LIVE_HOST:
+            it[0][name] = hb + r.layout[name][0]
+        for name in LIVE_DEV:
+            it[0][name] = db + r.dev_layout[name][0]
+        if self.pixels_in_place(r):
+            it[0]["rgb"] = r.rgb.data_ptr()
+        elif r.n_pixels:
+            off, size = r.layout["rgb"]
+            src = r.rgb if not isinstance(r.rgb, np.ndarray) else self.torch.from_numpy(np.ascontiguousarray(r.rgb))
+            self.host[r.block + off:r.block + off + size].copy_(src.reshape(-1))
+        cap = max(0, min(r.n_pixels, 1 << 24))
+        it[0]["n_pixels"], it[0]["seed"], it[0]["eps"] = r.n_pixels, r.seed, r.eps
+        it[0]["lbg_eps"], it[0]["lbg_conv_eps"], it[0]["lbg_max_iter"] = 1.0, r.eps, r.max_iter
+        it[0]["K"], it[0]["scheme"] = r.K, kq.INIT[r.scheme]
+        it[0]["max_iter"], it[0]["capacity"] = r.max_iter, cap
+        cls = 0 if r.n_pixels > self.split else 1
+        seq = self.q.publish(cls, it[0])
+        return None if seq is None else (cls, seq)
+
+    def done(self, cls: int, seq: int) -> bool:
+        return self.q.done(cls, seq)
+
+    def collect(self, r: Request) -> None:
+        kq = self.kq
+        h = self.host.numpy()
+
+        def get(name):
+            off, size = r.layout[name]
+            return h[r.block + off:r.block + off + size].copy()
+        r.idx = get("idx")
+        r.palette = get("palette").reshape(-1, 3)
+        r.centers = get("centers").view(np.float64).reshape(-1, 3)
+        r.result = np.frombuffer(get("result").tobytes(), dtype=kq.BATCH_RESULT_DTYPE)[0]
+
+    def close(self) -> None:
+        self.q.close()
+        self.stream.synchronize()

@@ -86,3 +86,29 @@ def test_lone_requests_take_the_whole_gpu_and_agree_within_tolerance():
             assert np.array_equal(a.palette, r.palette)
             assert np.max(np.abs(a.centers - r.centers)) <= 1e-3
     assert alone_be.solo_waves == len(mix)
+
+
+def test_live_server_same_result_as_alone():
+    """Requests admitted into a running launch (LiveServer) give exactly the
+    results they give alone, with memory admitting a few at a time and a
+    four-slot queue ring."""
+    require_cuda()
+    C = kq.kq_batch_max_cluster()
+    be = serve.LiveBackend(cluster=min(C, 4), split_pixels=30000, idle_us=5000, capacity=4)
+    lay = [serve.live_layout(h * w, K, kq.kq_batch_scratch_bytes, False) for h, w, K, _ in SIZES]
+    srv = serve.LiveServer(be, pool_bytes=3 * max(x[3] for x in lay), host_bytes=3 * max(x[1] for x in lay))
+    mix = _requests()
+    stats = serve.run_trace(srv, mix)
+    be.close()
+    # memory bounds what is in flight (small requests pack more densely than the largest)
+    assert stats["requests"] == len(SIZES) and srv.max_inflight >= 2
+    assert srv.host_arena.peak <= srv.host_arena.size and srv.dev_arena.peak <= srv.dev_arena.size
+    assert srv.host_arena.in_use == 0 and srv.dev_arena.in_use == 0
+    one = max(serve.request_layout(h * w, K, kq.kq_batch_scratch_bytes)[1] for h, w, K, _ in SIZES)
+    alone_srv = serve.Server(serve.CudaBackend(cluster=min(C, 4), split_pixels=30000), one, streams=1, max_wave=1)
+    for r in mix:
+        a = serve.Request(rid=r.rid, rgb=r.rgb, K=r.K, scheme=r.scheme, seed=r.seed)
+        alone_srv.submit(a)
+        alone_srv.drain()
+        assert r.result["status"] == kq.KQ_OK
+        assert _fields(a) == _fields(r), r.rid

@@ -185,3 +185,138 @@ def test_whole_gpu_lane_keeps_solo_slots_requests_in_flight():
     srv.drain()
     assert be.solo == [0, 1, 2] and srv.solo_inflight == 0
     assert sorted(r.rid for r in srv.finished) == [0, 1, 2]
+
+
+class FakeLiveBackend:
+    """A live launch on the host: items publish into a ring of `capacity` slots
+    per class and finish `work` steps after they were published; the launch
+    'runs' until `idle` steps pass without items in flight."""
+
+    def __init__(self, capacity=4, work=2, idle=3, split=1000):
+        self.capacity, self.work, self.idle, self.split = capacity, work, idle, split
+        self.launches = 0
+        self.running_for = 0
+
+    def scratch_bytes(self, cap):
+        return 0
+
+    def pixels_in_place(self, r):
+        return False
+
+    def setup(self, pool_bytes, host_bytes):
+        self.tail = [0, 0]
+        self.slot = [[None] * self.capacity, [None] * self.capacity]  # (seq, steps left)
+        self.collected = []
+
+    def tick(self):
+        for c in (0, 1):
+            for j, v in enumerate(self.slot[c]):
+                if v is not None and v[1] > 0:
+                    self.slot[c][j] = (v[0], v[1] - 1)
+        self.running_for = max(0, self.running_for - 1)
+
+    def ensure_running(self):
+        if self.running_for == 0:
+            self.launches += 1
+        self.running_for = self.idle
+
+    def publish(self, r):
+        c = 0 if r.n_pixels > self.split else 1
+        t = self.tail[c]
+        j = t % self.capacity
+        old = self.slot[c][j]
+        if old is not None and old[1] > 0:
+            return None  # the slot's item is not done
+        self.slot[c][j] = (t, self.work)
+        self.tail[c] += 1
+        return (c, t)
+
+    def done(self, c, seq):
+        v = self.slot[c][seq % self.capacity]
+        return v is not None and v[0] == seq and v[1] == 0
+
+    def collect(self, r):
+        self.collected.append(r.rid)
+
+
+def _live_reqs(sizes):
+    return [serve.Request(rid=i, rgb=np.zeros(3 * n, np.uint8), K=8) for i, n in enumerate(sizes)]
+
+
+def test_live_server_admits_in_order_by_memory_and_ring():
+    be = FakeLiveBackend(capacity=2, work=2)
+    host_one = serve.live_layout(100, 8, be.scratch_bytes, False)[1]
+    srv = serve.LiveServer(be, pool_bytes=1 << 20, host_bytes=3 * host_one)
+    for r in _live_reqs([100] * 5):
+        srv.submit(r)
+    srv.step()
+    # the ring of class 1 has two slots: two items published, the rest wait
+    assert sorted(srv.inflight) == [(1, 0), (1, 1)] and len(srv.waiting) == 3 and be.launches == 1
+    for _ in range(3):
+        be.tick()
+        srv.step()
+    assert [r.rid for r in srv.finished][:2] == [0, 1]
+    while not srv.idle():
+        be.tick()
+        srv.step()
+    assert [r.rid for r in srv.finished] == [0, 1, 2, 3, 4]
+    assert be.collected == [0, 1, 2, 3, 4]
+    assert srv.host_arena.in_use == 0 and srv.dev_arena.in_use == 0
+    assert srv.max_inflight <= 2
+
+
+def test_live_server_blocks_on_memory_without_overtaking():
+    be = FakeLiveBackend(capacity=8, work=3)
+    big = serve.live_layout(1000, 8, be.scratch_bytes, False)[1]
+    small = serve.live_layout(10, 8, be.scratch_bytes, False)[1]
+    srv = serve.LiveServer(be, pool_bytes=1 << 20, host_bytes=big + 256)  # < big + small
+    for r in _live_reqs([10, 1000, 10]):
+        srv.submit(r)
+    srv.step()
+    # the large request does not fit beside the first small one; the second small
+    # one, behind it, is not admitted first
+    assert list(srv.inflight.values())[0].rid == 0 and len(srv.inflight) == 1
+    assert [r.rid for r in srv.waiting] == [1, 2]
+    while not srv.idle():
+        be.tick()
+        srv.step()
+    assert [r.rid for r in srv.finished] == [0, 1, 2]
+
+
+def test_live_server_retires_an_item_whose_slot_was_reused():
+    # an item finishes, but the server has not seen its mark when the next
+    # publication takes its slot: it is retired at that moment
+    be = FakeLiveBackend(capacity=1, work=1)
+    real_done = be.done
+    be.done = lambda c, seq: False  # the marks stay unseen
+    srv = serve.LiveServer(be, pool_bytes=1 << 20, host_bytes=1 << 20)
+    reqs = _live_reqs([50, 50])
+    srv.submit(reqs[0])
+    srv.step()
+    be.tick()  # item 0 is done
+    srv.submit(reqs[1])
+    srv.step()  # publishing item 1 reuses item 0's slot
+    assert [r.rid for r in srv.finished] == [0] and list(srv.inflight) == [(1, 1)]
+    be.done = real_done
+    while not srv.idle():
+        be.tick()
+        srv.step()
+    assert [r.rid for r in srv.finished] == [0, 1]
+
+
+def test_live_server_relaunches_after_idle_exit():
+    be = FakeLiveBackend(capacity=4, work=1, idle=2)
+    srv = serve.LiveServer(be, pool_bytes=1 << 20, host_bytes=1 << 20)
+    srv.submit(_live_reqs([20])[0])
+    while not srv.idle():
+        be.tick()
+        srv.step()
+    for _ in range(4):
+        be.tick()  # the launch leaves after its idle limit
+    r = _live_reqs([20])[0]
+    r.rid = 7
+    srv.submit(r)
+    while not srv.idle():
+        be.tick()
+        srv.step()
+    assert be.launches == 2 and [x.rid for x in srv.finished] == [0, 7]
