@@ -482,6 +482,20 @@ def run_serving(args, rank, world, local) -> None:
     waves, solo_waves = srv.waves, srv.backend.solo_waves
     del srv
     torch.cuda.empty_cache()
+    # admission into a running launch (live queue), on the same trace
+    lbe = serve.LiveBackend(cluster, split, device=dev, idle_us=20000, capacity=4096)
+    lsrv = serve.LiveServer(lbe, pool_bytes, 4 << 30)
+    for r in requests(8):
+        lsrv.submit(r)
+    lsrv.drain()
+    lsrv.finished.clear()
+    lreqs = requests()
+    lout = serve.run_trace(lsrv, lreqs)
+    lsame = sum(int(a.result["sse_num"]) == int(b.result["sse_num"]) for a, b in zip(reqs, lreqs))
+    llaunches = lbe.launches
+    lbe.close()
+    del lsrv, lbe
+    torch.cuda.empty_cache()
     # the plain per-image path behind the same scheduler, on the same trace
     plain = serve.Server(serve.PlainBackend(max_px, device=dev), 1 << 30, streams=1, max_wave=1)
     preqs = requests()
@@ -503,6 +517,9 @@ def run_serving(args, rank, world, local) -> None:
             "gpu_launches": None,
             "p50_ms": out["p50_ms"], "img_per_s": out["img_per_s"], "mpix_per_s": out["mpix_per_s"],
             "waves": waves, "solo_waves": solo_waves,
+            "live_server": {"p50_ms": lout["p50_ms"], "p99_ms": lout["p99_ms"], "img_per_s": lout["img_per_s"],
+                            "mpix_per_s": lout["mpix_per_s"], "launches": llaunches, "same_sse_requests": lsame,
+                            "note": "requests admitted into one running launch (kq_live_*); no whole-GPU lane"},
             "per_image_path": {"p50_ms": pout["p50_ms"], "p99_ms": pout["p99_ms"], "img_per_s": pout["img_per_s"],
                                "same_sse_requests": same}}
     if rank == 0:
