@@ -339,7 +339,8 @@ KQ_API int kq_live_reset(void *ws, size_t ws_bytes, kq_stream_t stream);
 /* Host: publishes a copy of *item (host memory) in class `cls` and returns its
  * sequence number in *h_seq.  KQ_ECAPACITY when the ring slot it needs still holds
  * an item that is not done; KQ_EINVAL for an invalid item, as kq_batch_plan checks
- * them, or after kq_live_close. */
+ * them, or after kq_live_close.  One host thread publishes at a time (the tail is
+ * read and then advanced without a lock). */
 KQ_API int kq_live_publish(kq_live_queue *q, int32_t cls, const kq_batch_item *item, int64_t *h_seq);
 
 /* Host: 1 when item `seq` of class `cls` is done (its outputs are written), else 0.
@@ -354,7 +355,9 @@ KQ_API int kq_live_close(kq_live_queue *q);
 
 /* Launches the persistent live kernel on `stream` (asynchronous): cfg->cluster
  * CTAs per group for class 0 (cfg->split_pixels is not used: the publisher picks
- * the class), idle limit `idle_us` (>= 1). */
+ * the class), idle limit `idle_us` (>= 1).  KQ_EINVAL when `q` is not page-locked
+ * host memory the device can reach; KQ_ENOMEM when `ws` is smaller than
+ * kq_batch_workspace_size(). */
 KQ_API int kq_live_run(kq_live_queue *q, const kq_batch_config *cfg, uint32_t idle_us, void *ws, size_t ws_bytes,
                        kq_stream_t stream);
 
