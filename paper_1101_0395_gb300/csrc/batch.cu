@@ -15,6 +15,14 @@
 // single-image kernels (the same dist3, the same integer seeding, the same Lloyd
 // body), so results agree with kq_histogram/kq_seed/kq_lloyd/kq_map up to the
 // FP32 summation order of the SSE, whose block partition differs.
+//
+// A live launch (batch_live_kernel) runs the same groups on images that arrive
+// while it runs: the host publishes items into a queue in page-locked host memory,
+// groups claim them through counters in the workspace header and post a done mark
+// per item; a group with nothing to take waits with a bounded idle limit.  The
+// Wu moments, which the group's threads rewrite step by step, are read through L2
+// (__ldcg), as the batched steps' other cross-thread reads are: through L1 they
+// were seen stale in a live launch, which runs many images on one SM.
 #include <math.h>
 #include <stddef.h>
 #include <string.h>
