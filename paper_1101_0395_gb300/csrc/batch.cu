@@ -21,7 +21,7 @@
 // groups claim them through counters in the workspace header and post a done mark
 // per item; a group with nothing to take waits with a bounded idle limit.  The
 // Wu moments, which the group's threads rewrite step by step, are read through L2
-// (__ldcg), as the batched steps' other cross-thread reads are: through L1 they
+// (__ldcg), as most of the batched steps' cross-thread reads are: through L1 they
 // were seen stale in a live launch, which runs many images on one SM.
 #include <math.h>
 #include <stddef.h>
